@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free H x on GB300.
+
+One step = one pass of the hot path: y = H x for the mixed-spin ferrimagnetic
+open chain (N=20, alternating s=1/2 and s=1, D = 2^10 3^10 = 60,466,176),
+FP64 storage, one right-hand side, inputs resident in HBM. x and y (968 MB)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0). Extra keys report the other forms of the path
+against this plain FP64 kernel: FP32 storage, the 1.07e9-state
+Tavis-Cummings apply, the batched persistent launch, the adjoint, and the
+Lanczos ground-state energy in FP32 vs FP64 storage.
+
+--impl reference times the CPU oracle (the reference arm of this build) on
+a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·x Gstates/s & HBM GB/s vs peak; batched/FP32/adjoint vs plain FP64"
+WORKLOAD = "ferrimagnet_chain_n20"
+WORKLOAD_DESC = ("mixed-spin open chain N=20 alternating s=1/2,1 (D=2^10*3^10=60466176), "
+                 "Heisenberg J=1, h_z=0.1, D_i~U[-0.5,0.5] on spin-1 sites")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("apply.cu", "device_common.cuh", "plan.cpp", "hm_internal.h"):
+        with open(os.path.join(ROOT, "paper_2606_02169_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel sources changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        rec = t.get(key)
+        if rec and rec.get("source_hash") == kernel_source_hash():
+            return rec["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # nvidia-smi's start-up can stall kernel submission: time only
+            # after it has produced samples
+            t0 = time.time()
+            while time.time() - t0 < 15:
+                with open(self.path) as f:
+                    if sum(1 for _ in f) >= 3:
+                        break
+                time.sleep(0.05)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [v.strip() for v in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                    pw.append(float(c[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+def dist():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as td
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed(fn, steps, warmup, ws, stream):
+    """Total ms of `steps` calls of fn, CUDA events on the launching stream,
+    barrier + synchronize on both sides, max over ranks."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    return max_over_ranks(e0.elapsed_time(e1), ws)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): bounded row samples
+# ---------------------------------------------------------------------------
+
+def oracle_rate(model, seconds, threads=0):
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    D = oracle.dimension(model.sites)
+    x = W.vector(D, 3)
+    oracle.build()
+    nthreads = threads or len(os.sched_getaffinity(0))
+    r0 = 20000
+    t0 = time.perf_counter()
+    oracle.apply(model.sites, model.terms, x, row_begin=0, row_end=r0, nthreads=nthreads)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    rows = int(min(D, max(r0, r0 * seconds / dt)))
+    start = (D - rows) // 2
+    t0 = time.perf_counter()
+    oracle.apply(model.sites, model.terms, x, row_begin=start, row_end=start + rows, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return rows / dt / 1e9, rows, dt, nthreads
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    m = W.ferrimagnet_chain(20)
+    D = oracle.dimension(m.sites)
+    x = W.vector(D, 3)
+    oracle.build()
+    nthreads = len(os.sched_getaffinity(0))
+    budget = 120.0 / max(1, args.steps + args.warmup)    # whole run within a few minutes
+    t0 = time.perf_counter()
+    oracle.apply(m.sites, m.terms, x, row_begin=0, row_end=20000, nthreads=nthreads)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    rows = int(min(D, max(20000, 20000 * min(budget, 5.0) / dt)))
+    start = (D - rows) // 2
+    for _ in range(args.warmup):
+        oracle.apply(m.sites, m.terms, x, row_begin=start, row_end=start + rows, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply(m.sites, m.terms, x, row_begin=start, row_end=start + rows, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    val = rows * args.steps / dt / 1e9
+    sample = f"rows [{start}, {start + rows}) of {D} per step ({rows / D:.3%} of one H x)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gstates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 * D / rows,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "D": D, "nvec": 1},
+        "cpu_baseline": {"value": val, "unit": "Gstates/s", "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Gstates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2606_02169_gb300 import Batch, Hamiltonian
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
+
+    m = W.ferrimagnet_chain(20)
+    h = Hamiltonian(m.sites, m.terms)
+    D = h.D
+    x = W.torch_vector(D, 3 + rank, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+
+    clocks = Clocks(local)
+    for _ in range(args.warmup):
+        h.apply(x, out=y)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms = timed(lambda: h.apply(x, out=y), args.steps, 0, ws, stream)
+    clk = clocks.stop()
+    ms_step = ms / args.steps
+    value = ws * D / (ms_step * 1e-3) / 1e9
+    bytes_alg = 16.0 * D
+    achieved = bytes_alg / (ms_step * 1e-3) / 1e9
+    traffic = recorded_traffic("k_apply_df64_" + WORKLOAD)
+
+    # end to end through the public API: pinned host x -> device, apply, y -> pinned host
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        h.apply(xd, out=y)
+        yh.copy_(y, non_blocking=True)
+
+    k_e2e = max(3, min(args.steps, 50))
+    ms_e2e = timed(e2e_step, k_e2e, 3, ws, stream)
+    e2e_val = ws * D / (ms_e2e / k_e2e * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gstates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "D": D, "nvec": 1,
+                   "l2": "inputs larger than L2 (x+y = 968 MB per step), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": {"value": e2e_val, "unit": "Gstates/s", "h2d_bytes_per_step": 8 * D,
+                "d2h_bytes_per_step": 8 * D, "steps": k_e2e},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_apply<df64> (FP64 storage, FP32-pair arithmetic)",
+                     "algorithmic_bytes_per_launch": bytes_alg,
+                     "algorithmic_bytes_per_state": 16},
+        "clocks": clk,
+    }
+
+    if rank == 0 and ws == 1 and not args.skip_variants:
+        line["variants"] = variants(args, h, m, x, y, ms_step, stream, hbm)
+
+    if rank == 0:
+        rate, rows, dt, nth = oracle_rate(m, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "Gstates/s", "cores": nth, "kind": "oracle",
+                                "sample": f"{rows} contiguous target rows of {D} ({dt:.1f} s, "
+                                          f"C oracle with OpenMP)"}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+def variants(args, h, m, x, y, ms_f64, stream, hbm):
+    import torch
+
+    import workloads as W
+    from paper_2606_02169_gb300 import Batch, Hamiltonian
+    out = {}
+    steps = max(20, min(args.steps, 200))
+    D = h.D
+
+    # FP32 storage on the same workload
+    xf = x.float()
+    yf = torch.empty_like(xf)
+    ms = timed(lambda: h.apply(xf, out=yf), steps, 5, 1, stream) / steps
+    out["fp32_storage"] = {"gstates_s": D / ms / 1e6, "ms": ms, "speedup_vs_f64": ms_f64 / ms,
+                           "hbm_frac": 8 * D / ms / 1e6 / hbm}
+    # native FP64 arithmetic (the plain port) on the same workload
+    ms = timed(lambda: h.apply_ex(x, out=y, native_f64=True), max(5, steps // 4), 2, 1, stream) / max(5, steps // 4)
+    out["native_fp64_arith"] = {"gstates_s": D / ms / 1e6, "ms": ms, "slowdown_vs_df64": ms / ms_f64}
+    del xf, yf
+
+    # Lanczos ground state: FP32 vs FP64 storage (same v0, 100 steps, local reorth)
+    v0 = W.torch_vector(D, 11, dtype=torch.float64)
+    t0 = time.perf_counter()
+    r64 = h.lanczos(v0, 100, reorth=True)
+    t64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r32 = h.lanczos(v0.float(), 100, reorth=True)
+    t32 = time.perf_counter() - t0
+    out["lanczos_100"] = {"e0_f64": r64["e0"], "e0_f32": r32["e0"], "abs_dE0_f32_vs_f64": abs(r32["e0"] - r64["e0"]),
+                          "s_f64": t64, "s_f32": t32}
+    del v0
+
+    # Tavis-Cummings, D = 2^30 (boson last), FP32 and FP64
+    mt = W.tavis_cummings(24, 64, seed=7)
+    ht = Hamiltonian(mt.sites, mt.terms)
+    Dt = ht.D
+    for name, dt, esz in (("tc_1e9_f32", torch.float32, 4), ("tc_1e9_f64", torch.float64, 8)):
+        xt = W.torch_vector(Dt, 8, dtype=dt)
+        yt = torch.empty_like(xt)
+        k = 10
+        ms = timed(lambda: ht.apply(xt, out=yt), k, 2, 1, stream) / k
+        out[name] = {"gstates_s": Dt / ms / 1e6, "ms": ms, "hbm_frac_algorithmic": 2 * esz * Dt / ms / 1e6 / hbm}
+        del xt, yt
+        torch.cuda.empty_cache()
+    del ht
+
+    # batched disorder ensemble: 256 XXZ spin-1 chains N in 8..14, 16 RHS, FP32
+    models = W.disorder_ensemble(256, 8, 14, 1000)
+    hams = [Hamiltonian(mm.sites, mm.terms) for mm in models]
+    nvec = 16
+    xs = [W.torch_vector(hh.D * nvec, 1000 + i, dtype=torch.float32, normalize=False) for i, hh in enumerate(hams)]
+    ys = [torch.empty_like(t) for t in xs]
+    total = sum(hh.D for hh in hams) * nvec
+    b = Batch(hams)
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        b.apply(xs, ys, stream=s2)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s2):
+        b.apply(xs, ys, stream=s2)
+    k = 5
+    ms_b = timed(lambda: g.replay(), k, 1, 1, stream) / k
+
+    def plain():
+        for hh, xx, yy in zip(hams, xs, ys):
+            hh.apply(xx, out=yy)
+
+    ms_p = timed(plain, k, 1, 1, stream) / k
+    out["batched_256_chains_16rhs_f32"] = {
+        "states_x_rhs": total, "gstates_s_batched_graph": total / ms_b / 1e6,
+        "gstates_s_per_instance_launches": total / ms_p / 1e6, "speedup": ms_p / ms_b,
+        "hbm_frac_batched": 8 * total / ms_b / 1e6 / hbm}
+    del xs, ys, b, hams, g
+    torch.cuda.empty_cache()
+
+    # adjoint on the 4x5 lattice (D = 2^20, FP64): H^T gy + 113 coupling gradients
+    ml = W.square_lattice_xxz(4, 5, seed=4)
+    hl = Hamiltonian(ml.sites, ml.terms)
+    xl = W.torch_vector(hl.D, 5, dtype=torch.float64)
+    gl = W.torch_vector(hl.D, 6, dtype=torch.float64)
+    yl = torch.empty_like(xl)
+    gx = torch.empty_like(xl)
+    gc = torch.empty(hl.nterms, dtype=torch.float64, device="cuda")
+    k = 50
+    ms_fwd = timed(lambda: hl.apply(xl, out=yl), k, 5, 1, stream) / k
+    ms_adj = timed(lambda: hl.adjoint(gl, xl, gx=gx, gcoef=gc), k, 5, 1, stream) / k
+    ms_grad = timed(lambda: hl.adjoint(gl, xl, want_gx=False, gcoef=gc), k, 5, 1, stream) / k
+    out["adjoint_4x5_f64"] = {"ms_forward": ms_fwd, "ms_adjoint_gx_and_gcoef": ms_adj,
+                              "ms_gcoef_only": ms_grad, "adjoint_over_forward": ms_adj / ms_fwd,
+                              "nterms": hl.nterms}
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

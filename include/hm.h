@@ -1,0 +1,175 @@
+/*
+ * hm.h -- C ABI of the GB300 matrix-free spin / truncated-boson Hamiltonian
+ * library (y = H x on the full tensor-product basis, mixed-radix indexed).
+ *
+ * Operation (from "Spin Hamiltonian as Matrix-Free Linear Map"):
+ *   sites k = 0..N-1 with local dimension d_k (spin: d = 2s+1, Sec. I Eq. 1;
+ *   truncated boson: d = n_max+1, App. C). Basis index
+ *     I = sum_k n_k M_k,  M_k = prod_{l>k} d_l           (Sec. III Eq. encode)
+ *   site 0 is the MOST significant digit; local digit n = m + s, so n = 0 is
+ *   m = -s (Sec. II notation guide). Bosons: n = occupation.
+ *   H = sum_t coef_t op_i(t)(site i) op_j(t)(site j)    (Sec. IV Eq. pairham,
+ *   App. B higher powers, App. C spin-boson terms), applied target-driven:
+ *     y_F = <F|H|x> = sum over channels of coef * Lambda * Lambda * x_{F+offset}
+ *   (Sec. II, Sec. IV.B Eq. sourceoffset, App. A).
+ *
+ * Vectors: caller-owned DEVICE pointers, state-major interleaved: element v
+ * of state k is at [k*nvec + v]. Real storage only (HM_F64 / HM_F32).
+ * Every call is asynchronous on the given CUDA stream (NULL = legacy default
+ * stream) unless stated otherwise. Plans are library-owned; a plan may be used
+ * from several streams at once, but hm_set_coefficients must not overlap
+ * applies of the same plan.
+ *
+ * Errors: every int-returning call returns HM_OK (0) or a negative HM_ERR_*;
+ * hm_strerror() names a code and hm_last_error() returns a thread-local text
+ * with details of the most recent failure on the calling thread.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_plan* hm_handle;
+
+/* site kinds */
+enum { HM_SPIN = 0, HM_BOSON = 1 };
+
+typedef struct {
+    int32_t kind;  /* HM_SPIN or HM_BOSON */
+    int32_t dim;   /* spin: 2s+1 >= 2; boson: n_max+1 >= 2 */
+} hm_site;
+
+/* local operators (Sec. IV.A, App. B, App. C) */
+enum {
+    HM_ID = 0,   /* identity                                          */
+    HM_SZ = 1,   /* S_z                                  (q = 0)       */
+    HM_SX = 2,   /* S_x = (S+ + S-)/2   (Sec. IV.A h_+- split)          */
+    HM_SY = 3,   /* S_y = (S+ - S-)/(2i); imaginary alone: needs pairing */
+    HM_SP = 4,   /* S_+                                  (q = +1)      */
+    HM_SM = 5,   /* S_-                                  (q = -1)      */
+    HM_SZ2 = 6,  /* S_z^2                                (App. B q = 0)*/
+    HM_SP2 = 7,  /* S_+^2                                (App. B q = +2)*/
+    HM_SM2 = 8,  /* S_-^2                                (App. B q = -2)*/
+    HM_N = 9,    /* boson a^dagger a                     (App. C)      */
+    HM_A = 10,   /* boson a                              (q = -1)      */
+    HM_ADAG = 11 /* boson a^dagger                       (q = +1)      */
+};
+
+/* One term: coef * op_i(site_i) * op_j(site_j); site_j = -1 for a
+ * single-site term (op_j ignored). site_i != site_j. Duplicates add. */
+typedef struct {
+    int32_t site_i, op_i, site_j, op_j;
+    double coef;
+} hm_term;
+
+typedef enum { HM_F64 = 0, HM_F32 = 1 } hm_dtype;
+
+/* return codes */
+enum {
+    HM_OK = 0,
+    HM_ERR_INVALID_ARG = -1,      /* bad site/op kind, i == j, null pointer, nvec < 1 */
+    HM_ERR_OVERFLOW = -2,         /* D >= 2^62                                      */
+    HM_ERR_ALIAS = -3,            /* x and y overlap                                */
+    HM_ERR_COMPLEX_REQUIRED = -4, /* the term list has an imaginary matrix element  */
+    HM_ERR_NOT_HERMITIAN = -5,    /* Lanczos on a non-self-adjoint term list        */
+    HM_ERR_CUDA = -6,             /* CUDA runtime error (text in hm_last_error)      */
+    HM_ERR_OOM = -7,              /* device allocation failed                       */
+    HM_ERR_TIMEOUT = -8,          /* a bounded device wait gave up                  */
+    HM_ERR_UNSUPPORTED = -9,      /* shape outside the implemented limits           */
+    HM_ERR_TOO_LARGE = -10,       /* size above a documented fixed maximum          */
+    HM_LANCZOS_BREAKDOWN = 1      /* warning: Krylov space exhausted early          */
+};
+
+/* Build a plan (host call; allocates the plan's small device tables on the
+ * current device and synchronises). sites[nsites], terms[nterms] are read and
+ * copied. Limits: 1 <= nsites <= 64, D = prod d_k < 2^62, each d_k <= 65536.
+ * Cost O(N + |terms|) plus O(B) tables for the low-digit block (B <= 4096). */
+int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
+              hm_handle* out);
+
+/* Replace all term coefficients (host array of nterms doubles) without
+ * re-planning (Sec. VII: repeatedly rebuilt Hamiltonians). Synchronous. The
+ * new list must not make any matrix element imaginary; channels whose
+ * coefficient was exactly zero at create time stay present. */
+int hm_set_coefficients(hm_handle h, const double* coefs);
+
+/* D = prod d_k (Sec. I Eq. 1), or a negative code for a NULL handle. */
+int64_t hm_dim(hm_handle h);
+int32_t hm_num_terms(hm_handle h);
+
+/* y = H x for nvec right-hand sides (x, y: device, D*nvec elements of dtype;
+ * x read-only, y fully overwritten; x and y must not overlap). Each output
+ * element is owned by exactly one GPU lane (pull form, Sec. II): no atomics,
+ * bit-reproducible run to run. */
+int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream);
+
+/* Diagnostic variant of hm_apply. flags bit 0: native FP64 arithmetic for
+ * HM_F64 (default: FP64 values split into FP32 pairs, accumulated as a
+ * double-float sum with error-free transformations; ~2^-46 relative);
+ * bit 1: apply H^T instead of H. ctas > 0 forces the persistent grid size
+ * (0 = library default). Same ownership and error rules as hm_apply. */
+int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
+                int32_t ctas, void* stream);
+
+/* Adjoint / gradient pass (reverse mode of y = H(c) x):
+ *   gx[k*nvec+v] = (H^T gy)                     if gx != NULL (overwritten)
+ *   gcoef[t]     = sum_v <gy_v| O_t |x_v>        if gcoef != NULL (device,
+ *                  nterms doubles, overwritten), O_t = op_i op_j without coef.
+ * gy, x: device vectors of dtype. gcoef is always FP64, reduced
+ * deterministically (fixed-order two-pass reduction, no atomics). Uses
+ * library-owned scratch of O(nterms * grid) doubles per plan; calls on the
+ * same plan must not overlap on the GPU. */
+int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
+                     int64_t nvec, hm_dtype dtype, void* stream);
+
+/* Lanczos ground state (Sec. I: Krylov solvers need only y = H x).
+ * v0: device start vector (D elements of dtype, need not be normalised).
+ * Runs up to `steps` steps; alpha/beta (host, >= steps doubles) receive the
+ * tridiagonal matrix (FP64 dot products even for HM_F32 storage), *steps_done
+ * the number of alpha values, *e0 the lowest Ritz value (FP64 host
+ * tridiagonal eigensolver). If psi0_out (device, D elements) is not NULL the
+ * recurrence is re-run from v0 to assemble the normalised Ritz vector without
+ * storing the Krylov basis. Synchronous on `stream`. flags: bit 0 = local
+ * reorthogonalisation against v_{k-1} and v_k (default off = plain
+ * three-term recurrence). Returns HM_LANCZOS_BREAKDOWN (> 0) when beta_k
+ * falls below 1e-14 |alpha|max before `steps`. Allocates 3 (4 with psi0)
+ * work vectors per call. */
+int hm_lanczos(hm_handle h, const void* v0, int32_t steps, hm_dtype dtype, int32_t flags,
+               double* alpha, double* beta, int32_t* steps_done, void* psi0_out, double* e0,
+               void* stream);
+
+/* Batched apply over many plans of uneven size: one persistent launch walks a
+ * (instance, tile) work list. hs[n] stay owned by the caller and must outlive
+ * the batch. xs[b], ys[b]: device pointers (arrays of n pointers, host
+ * memory). All instances share nvec and dtype. */
+int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out);
+int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int64_t nvec,
+                   hm_dtype dtype, void* stream);
+
+/* Autotuner: time the apply variants for (nvec, dtype) on scratch vectors and
+ * cache the fastest in the plan (and in the process-wide cache keyed by the
+ * site-dimension signature). Synchronous. */
+int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
+
+/* Diagnostic, host only: run the host half of hm_create (validation,
+ * operator expansion, channel merging, high/low split, tables) without
+ * touching the GPU, and write the resulting tables as JSON text. which = 0
+ * exports H, 1 exports H^T. On success *len = bytes needed including the
+ * terminating NUL; the text is written only if buf != NULL and
+ * bufsize >= *len. Same error codes as hm_create. */
+int hm_plan_export(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
+                   int32_t which, char* buf, int64_t bufsize, int64_t* len);
+
+int hm_destroy(hm_handle h);
+const char* hm_strerror(int code);
+const char* hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H */

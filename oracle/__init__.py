@@ -233,7 +233,10 @@ def dense(sites, terms, coefs=None, sparse=False):
     if sparse:
         import scipy.sparse as sp
         H = sp.csr_matrix((D, D), dtype=np.complex128)
-        kron, eye = sp.kron, (lambda d: sp.identity(d, dtype=np.complex128, format="csr"))
+        # format="csr" keeps scipy on its COO path (nnz(A) * nnz(B) entries);
+        # its default BSR path stores dense blocks including explicit zeros
+        kron = lambda a, b: sp.kron(a, b, format="csr")
+        eye = lambda d: sp.identity(d, dtype=np.complex128, format="csr")
     else:
         if D > 1 << 13:
             raise ValueError("dense assembly is for tiny systems (D <= 8192)")
@@ -245,11 +248,11 @@ def dense(sites, terms, coefs=None, sparse=False):
         factors[i] = local_matrix(sites[i][0], sites[i][1], oi)
         if j >= 0:
             factors[j] = local_matrix(sites[j][0], sites[j][1], oj)
+        if sparse:
+            factors = [sp.csr_matrix(f) for f in factors]
         M = factors[0]
         for f in factors[1:]:
             M = kron(M, f)
-            if sparse:
-                M = M.tocsr()
         H = H + cs[t] * M
     return H
 

@@ -1,0 +1,323 @@
+// extern "C" boundary of the hm library: argument validation, error codes and
+// dispatch to the plan builder and kernels. No torch types cross this line.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& s) { g_err = s; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? HM_ERR_OOM : HM_ERR_CUDA;
+}
+
+static Plan* as_plan(hm_handle h) {
+  Plan* p = reinterpret_cast<Plan*>(h);
+  if (!p || p->magic != 0x484d504cU) return nullptr;
+  return p;
+}
+
+cudaError_t apply_kplan(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt,
+                        cudaStream_t s, int ctas, bool native_f64);
+
+static size_t esize(hm_dtype dt) { return dt == HM_F32 ? 4 : 8; }
+
+static bool overlap(const void* a, const void* b, size_t bytes) {
+  auto pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+int check_vec_args(const Plan* p, const void* x, const void* y, long long nvec, hm_dtype dt) {
+  if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
+  if (p->is_batch) { set_error("batch handle given to a single-plan call"); return HM_ERR_INVALID_ARG; }
+  if (dt != HM_F64 && dt != HM_F32) { set_error("dtype must be HM_F64 or HM_F32"); return HM_ERR_INVALID_ARG; }
+  if (nvec < 1) { set_error("nvec must be >= 1"); return HM_ERR_INVALID_ARG; }
+  if (nvec > (1 << 19)) { set_error("nvec above 2^19 (a low block of B*nvec elements must stay below 2^31)"); return HM_ERR_UNSUPPORTED; }
+  if (!x || !y) { set_error("null vector pointer"); return HM_ERR_INVALID_ARG; }
+  if (((uintptr_t)x % esize(dt)) || ((uintptr_t)y % esize(dt))) {
+    set_error("vector pointers must be aligned to the element size");
+    return HM_ERR_INVALID_ARG;
+  }
+  if ((double)p->D * (double)nvec > 9.0e18) { set_error("D * nvec overflows int64"); return HM_ERR_OVERFLOW; }
+  if (overlap(x, y, (size_t)(p->D * nvec) * esize(dt))) {
+    set_error("x and y overlap (the pull form needs x read-only while y is written)");
+    return HM_ERR_ALIAS;
+  }
+  return HM_OK;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+static std::string tune_signature(const Plan* p, hm_dtype dt, long long nvec) {
+  std::string s = std::to_string((int)dt) + "/" + std::to_string(nvec) + "/";
+  for (auto& st : p->sites) s += std::to_string(st.dim) + ",";
+  s += "/" + std::to_string(p->k.n_hh) + "," + std::to_string(p->k.n_grp) + "," + std::to_string(p->k.n_mem) + "," + std::to_string(p->k.ell_w);
+  return s;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
+              hm_handle* out) {
+  if (!out) { set_error("out is NULL"); return HM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!sites || nsites < 1 || nterms < 0 || (nterms > 0 && !terms)) {
+    set_error("sites/terms arrays invalid");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (nsites > kMaxSites) { set_error("nsites must be in [1, 64]"); return HM_ERR_INVALID_ARG; }
+  Plan* p = new Plan();
+  p->N = nsites;
+  p->sites.assign(sites, sites + nsites);
+  p->terms.assign(terms, terms + nterms);
+  cudaGetDevice(&p->device);
+  int rc = plan_check(p);
+  if (rc == HM_OK) rc = build_plan(p);
+  if (rc != HM_OK) {
+    free_plan_device(p);
+    delete p;
+    return rc;
+  }
+  *out = reinterpret_cast<hm_handle>(p);
+  return HM_OK;
+}
+
+int hm_set_coefficients(hm_handle h, const double* coefs) {
+  Plan* p = as_plan(h);
+  if (!p || p->is_batch || !coefs) { set_error("invalid handle or coefficients"); return HM_ERR_INVALID_ARG; }
+  for (size_t t = 0; t < p->terms.size(); ++t)
+    if (!std::isfinite(coefs[t])) { set_error("non-finite coefficient"); return HM_ERR_INVALID_ARG; }
+  cudaError_t e = cudaDeviceSynchronize();  // no apply of the old tables may still run
+  if (e != cudaSuccess) return cuda_fail(e, "set_coefficients sync");
+  std::vector<hm_term> old = p->terms;
+  for (size_t t = 0; t < p->terms.size(); ++t) p->terms[t].coef = coefs[t];
+  int rc = build_plan(p);
+  if (rc != HM_OK) {
+    p->terms = old;
+    int rc2 = build_plan(p);
+    (void)rc2;
+  }
+  return rc;
+}
+
+int64_t hm_dim(hm_handle h) {
+  Plan* p = as_plan(h);
+  if (!p) return HM_ERR_INVALID_ARG;
+  return p->D;
+}
+
+int32_t hm_num_terms(hm_handle h) {
+  Plan* p = as_plan(h);
+  if (!p) return HM_ERR_INVALID_ARG;
+  return (int32_t)p->terms.size();
+}
+
+int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream) {
+  Plan* p = as_plan(h);
+  int rc = check_vec_args(p, x, y, nvec, dtype);
+  if (rc) return rc;
+  auto it = p->tuned.find({(int)dtype, (long long)nvec});
+  if (it == p->tuned.end() && !g_tune_cache.empty()) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto jt = g_tune_cache.find(tune_signature(p, dtype, nvec));
+    if (jt != g_tune_cache.end()) it = p->tuned.emplace(std::make_pair((int)dtype, (long long)nvec), jt->second).first;
+  }
+  return launch_apply(p, x, y, nvec, dtype, (cudaStream_t)stream, it == p->tuned.end() ? 0 : it->second);
+}
+
+int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
+                int32_t ctas, void* stream) {
+  Plan* p = as_plan(h);
+  int rc = check_vec_args(p, x, y, nvec, dtype);
+  if (rc) return rc;
+  const KPlan& k = (flags & 2) ? p->kt : p->k;
+  cudaError_t e = apply_kplan(k, x, y, nvec, dtype, (cudaStream_t)stream, ctas, (flags & 1) != 0);
+  if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+  return HM_OK;
+}
+
+int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
+                     int64_t nvec, hm_dtype dtype, void* stream) {
+  Plan* p = as_plan(h);
+  if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
+  if (!gx && !gcoef) return HM_OK;
+  if (gx) {
+    int rc = check_vec_args(p, gy, gx, nvec, dtype);
+    if (rc) return rc;
+  }
+  if (gcoef) {
+    int rc = check_vec_args(p, gy, x ? x : gy, nvec, dtype);
+    if (rc == HM_ERR_ALIAS) rc = HM_OK;  // gy and x may be the same vector
+    if (rc) return rc;
+    if (!x) { set_error("x is required for coupling gradients"); return HM_ERR_INVALID_ARG; }
+  }
+  return launch_adjoint(p, gy, x, gx, gcoef, nvec, dtype, (cudaStream_t)stream);
+}
+
+int hm_lanczos(hm_handle h, const void* v0, int32_t steps, hm_dtype dtype, int32_t flags,
+               double* alpha, double* beta, int32_t* steps_done, void* psi0_out, double* e0,
+               void* stream) {
+  Plan* p = as_plan(h);
+  if (!p || p->is_batch || !v0 || steps < 1 || !alpha || !beta || !steps_done || !e0) {
+    set_error("invalid Lanczos arguments");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (dtype != HM_F64 && dtype != HM_F32) { set_error("bad dtype"); return HM_ERR_INVALID_ARG; }
+  if (!p->hermitian) {
+    set_error("Lanczos needs a self-adjoint term list");
+    return HM_ERR_NOT_HERMITIAN;
+  }
+  int sd = 0;
+  int rc = run_lanczos(p, v0, steps, dtype, flags, alpha, beta, &sd, psi0_out, e0, (cudaStream_t)stream);
+  *steps_done = sd;
+  return rc;
+}
+
+int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out) {
+  if (!batch_out || !hs || n < 1) { set_error("invalid batch arguments"); return HM_ERR_INVALID_ARG; }
+  *batch_out = nullptr;
+  Plan* b = new Plan();
+  b->is_batch = true;
+  for (int i = 0; i < n; ++i) {
+    Plan* p = as_plan(hs[i]);
+    if (!p || p->is_batch) {
+      delete b;
+      set_error("batch member " + std::to_string(i) + " is not a plan handle");
+      return HM_ERR_INVALID_ARG;
+    }
+    b->members.push_back(p);
+  }
+  int rc = batch_setup(b);
+  if (rc) {
+    if (b->batch_dev) cudaFree(b->batch_dev);
+    delete b;
+    return rc;
+  }
+  *batch_out = reinterpret_cast<hm_handle>(b);
+  return HM_OK;
+}
+
+int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int64_t nvec,
+                   hm_dtype dtype, void* stream) {
+  Plan* b = as_plan(batch);
+  if (!b || !b->is_batch || !xs || !ys || nvec < 1) {
+    set_error("invalid batch apply arguments");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (dtype != HM_F64 && dtype != HM_F32) { set_error("bad dtype"); return HM_ERR_INVALID_ARG; }
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    int rc = check_vec_args(b->members[i], xs[i], ys[i], nvec, dtype);
+    if (rc) {
+      set_error("batch member " + std::to_string(i) + ": " + std::string(hm_last_error()));
+      return rc;
+    }
+  }
+  return launch_batch(b, xs, ys, nvec, dtype, (cudaStream_t)stream);
+}
+
+int hm_destroy(hm_handle h) {
+  Plan* p = as_plan(h);
+  if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
+  cudaDeviceSynchronize();
+  free_plan_device(p);
+  if (p->scratch) cudaFree(p->scratch);
+  if (p->batch_dev) cudaFree(p->batch_dev);
+  p->magic = 0;
+  delete p;
+  return HM_OK;
+}
+
+// Autotuner: time the apply over a ladder of grid sizes (persistent grids of
+// 1..16 CTAs per SM) on scratch vectors and keep the fastest per (dtype, nvec),
+// also in a process-wide cache keyed by the site dimensions and channel counts.
+int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
+  Plan* p = as_plan(h);
+  if (!p || p->is_batch || nvec < 1 || (dtype != HM_F64 && dtype != HM_F32)) {
+    set_error("invalid tune arguments");
+    return HM_ERR_INVALID_ARG;
+  }
+  const std::string sig = tune_signature(p, dtype, nvec);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      p->tuned[{(int)dtype, (long long)nvec}] = it->second;
+      return HM_OK;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->D * nvec * esize(dtype);
+  void *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "tune scratch x");
+  e = cudaMalloc(&y, bytes);
+  if (e != cudaSuccess) { cudaFree(x); return cuda_fail(e, "tune scratch y"); }
+  cudaMemsetAsync(x, 0, bytes, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_ctas = 0;
+  const int sms = num_sms();
+  int rc = HM_OK;
+  for (int per : {1, 2, 4, 8, 16}) {
+    const int ctas = sms * per;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4 && rc == HM_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = launch_apply(p, x, y, nvec, dtype, s, ctas);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = HM_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    if (rc != HM_OK) break;
+    if (tmin < best) { best = tmin; best_ctas = ctas; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (rc != HM_OK) return rc;
+  p->tuned[{(int)dtype, (long long)nvec}] = best_ctas;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_cache[sig] = best_ctas;
+  return HM_OK;
+}
+
+const char* hm_strerror(int code) {
+  switch (code) {
+    case HM_OK: return "ok";
+    case HM_ERR_INVALID_ARG: return "invalid argument";
+    case HM_ERR_OVERFLOW: return "dimension overflow (D >= 2^62)";
+    case HM_ERR_ALIAS: return "x and y overlap";
+    case HM_ERR_COMPLEX_REQUIRED: return "complex matrix elements with a real dtype";
+    case HM_ERR_NOT_HERMITIAN: return "term list is not self-adjoint";
+    case HM_ERR_CUDA: return "CUDA error";
+    case HM_ERR_OOM: return "out of device memory";
+    case HM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case HM_ERR_UNSUPPORTED: return "unsupported shape";
+    case HM_ERR_TOO_LARGE: return "size above the fixed maximum";
+    case HM_LANCZOS_BREAKDOWN: return "Lanczos breakdown (Krylov space exhausted)";
+    default: return "unknown error";
+  }
+}
+
+const char* hm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

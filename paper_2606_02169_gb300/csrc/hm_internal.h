@@ -1,0 +1,180 @@
+// Internal structures of the hm library (host plan + the POD block the
+// kernels receive by value). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <map>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hm.h"
+
+namespace hm {
+
+constexpr int kMaxSites = 64;
+constexpr int kLowBlockMax = 4096;  // low-digit block size bound (tables are O(B))
+constexpr int kMaxDim = 65536;      // largest local dimension accepted
+constexpr long long kMaxD = (1LL << 62) - 1;
+
+// Channel kinds for the per-tile channel list (high/low split of the digits).
+enum : uint8_t { CK_DIAG = 1, CK_SINGLE = 8 };
+
+// Channel on tile-uniform ("high") digits only: coefficient tab[n_i * dj + n_j]
+// indexed by TARGET digits, exactly zero where a source digit would leave
+// [0, d-1], so a zero coefficient doubles as the admissibility test of
+// Sec. IV.B. Its source offset is a multiple of the low-block size B.
+struct KChan {
+  long long off;   // source index = target index + off  (Eq. sourceoffset)
+  int tab;         // base of this channel's table in the coefficient pool
+  int dj;          // row length of the table (1 for single-site channels)
+  uint8_t si, sj;  // sites (sj = 255: single-site)
+  uint8_t kind;    // CK_* flags
+  uint8_t pad[5];
+};
+static_assert(sizeof(KChan) == 24, "KChan layout");
+
+// Channels on one high site h and one low site l whose coefficient factorises
+// as u(n_h) * v(n_l) are grouped by their low factor v:
+//   y_F += v(n_l(F)) * sum_{members m} u_m(n_h(F)) x_{F + off_m}
+// so a hop costs one load and one FMA. v(n_l) = 0 marks an inadmissible low
+// source digit, u_m(n_h) = 0 an inadmissible high one. A channel that does not
+// factorise forms a group of its own whose v row is selected per block by the
+// high digit (vstride > 0) and whose member has u = 1.
+struct KGroup {
+  int vtab;       // v table base in the pool
+  int vstride;    // 0: fixed v; else v row = vtab + n_vsite * vstride
+  int m0, m1;     // member range
+  uint8_t vsite;  // high site selecting the v row (255: none)
+  uint8_t lbit, lwid;  // low digit field
+  uint8_t pad;
+};
+static_assert(sizeof(KGroup) == 20, "KGroup layout");
+
+struct KMember {
+  long long off;  // source offset (0 for diagonal groups)
+  int utab;       // u table base, indexed by the digit of usite
+  uint8_t usite;
+  uint8_t pad[3];
+};
+static_assert(sizeof(KMember) == 16, "KMember layout");
+
+// Per-term channel used by the adjoint/gradient pass: like KChan, but every
+// site is resolved per lane (full digits), so it works for any split.
+struct KTermChan {
+  long long off;
+  int tab;      // base in the per-term coefficient pool
+  int dj;
+  int term;     // term index t
+  uint8_t si, sj;  // sites (sj = 255 for single-site)
+  uint8_t pad[2];
+};
+static_assert(sizeof(KTermChan) == 24, "KTermChan layout");
+
+struct KSite {
+  long long mh;   // high sites: multiplier relative to the low block, M_k / B
+  long long M;    // global multiplier M_k
+  int d;
+  uint8_t lbit, lwid, is_low, pad;
+};
+
+// Everything a kernel needs, passed by value (device pointers inside).
+struct KPlan {
+  long long D;      // dimension
+  long long nblk;   // D / B
+  int B;            // low-block size
+  int nsites, nhigh;
+  int n_hh_diag, n_hh;         // KChan list: [diag | off-diagonal]
+  int n_grp_diag, n_grp;       // KGroup list: [diag | off-diagonal]
+  int n_mem;                   // KMember list (all groups)
+  int ell_w;                   // width of the low-block ELL table
+  int nterm_ch;                // per-term channels (adjoint)
+  int nterms;
+  const KSite* sites;     // [nsites]
+  const KChan* ch;
+  const KGroup* grp;
+  const KMember* mem;
+  const uint32_t* ptab;   // [B] packed low digits of each low index
+  const int* ell_delta;   // [ell_w * B], w-major
+  const double* tab_d;    // coefficient pool (HH tables, u and v tables)
+  const float2* tab_df;
+  const float* tab_f;
+  const double* diag_d;   // [B] diagonal from low-only channels (+ constants)
+  const float2* diag_df;
+  const float* diag_f;
+  const double* ell_d;    // [ell_w * B]
+  const float2* ell_df;
+  const float* ell_f;
+  const KTermChan* tch;   // [nterm_ch]
+  const double* ttab_d;   // per-term tables
+  const float2* ttab_df;
+  const float* ttab_f;
+};
+
+struct Channel {            // host-side merged channel
+  int i = -1, j = -1;       // j = -1: single-site
+  int qi = 0, qj = 0;       // n_target = n_source + q
+  int di = 1, dj = 1;
+  std::vector<std::complex<double>> T;  // [di*dj], target-digit indexed
+  // the contributing products: T = sum_p a_p (x) b_p (coefficient folded into a)
+  std::vector<std::pair<std::vector<std::complex<double>>, std::vector<std::complex<double>>>> parts;
+};
+
+struct Plan {
+  uint32_t magic = 0x484d504cU;
+  int device = 0;
+  std::vector<hm_site> sites;
+  std::vector<hm_term> terms;
+  int N = 0;
+  long long D = 0;
+  std::vector<long long> M;
+  bool hermitian = false;
+
+  // split
+  int nlow = 0, B = 1;
+  long long nblk = 1;
+
+  KPlan k{};    // H
+  KPlan kt{};   // H^T (shares k's tables when H is symmetric)
+  void* dev = nullptr;        // one device allocation holding every table
+  size_t dev_bytes = 0;
+
+  // scratch for the adjoint reduction (grown on demand)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+
+  // autotuned grid size per (dtype, nvec); absent = default
+  std::map<std::pair<int, long long>, int> tuned;
+
+  // batch handle
+  bool is_batch = false;
+  std::vector<Plan*> members;
+  std::vector<unsigned long long> member_gen;
+  void* batch_dev = nullptr;
+  unsigned long long gen = 0;   // bumped by every (re)build of the tables
+};
+
+// plan.cpp
+int build_plan(Plan* p);            // (re)derive tables from sites/terms and upload
+void free_plan_device(Plan* p);
+int plan_check(const Plan* p);
+
+// error text (capi.cpp)
+void set_error(const std::string& s);
+int cuda_fail(cudaError_t e, const char* what);
+
+// kernels (apply.cu / adjoint.cu / lanczos.cu / batch.cu)
+int launch_apply(const Plan* p, const void* x, void* y, long long nvec, hm_dtype dt,
+                 cudaStream_t s, int ctas_override);
+int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
+                   long long nvec, hm_dtype dt, cudaStream_t s);
+int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,
+                double* beta, int* steps_done, void* psi0, double* e0, cudaStream_t s);
+int batch_setup(Plan* b);
+int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec, hm_dtype dt,
+                 cudaStream_t s);
+int num_sms();
+
+}  // namespace hm

@@ -1,0 +1,313 @@
+// Device Lanczos ground state (Sec. I: Krylov solvers consume only y = H x).
+//   w = H v_k;  alpha_k = <v_k, w>;  w -= alpha_k v_k + beta_{k-1} v_{k-1};
+//   [optional second Gram-Schmidt pass against v_k, v_{k-1}];
+//   beta_k = ||w||;  v_{k+1} = w / beta_k.
+// Dot products and norms accumulate in FP64 (even for FP32 storage) and are
+// reduced in a fixed order (per-block partials, then one block), so a rerun
+// from the same v0 reproduces every Krylov vector bit for bit. The ground
+// state Ritz vector is assembled in that rerun, so the Krylov basis is never
+// stored. Scalars live on the device between kernels: the step loop has no
+// host round trip. The tridiagonal eigenproblem is solved on the host in
+// FP64 (Sturm-sequence bisection for the lowest eigenvalue, then inverse
+// iteration with a partially pivoted tridiagonal solve for its vector).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace hm {
+
+cudaError_t apply_kplan(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt,
+                        cudaStream_t s, int ctas, bool native_f64);
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+template <class T>
+__device__ __forceinline__ double tod(T v);
+template <>
+__device__ __forceinline__ double tod<float>(float v) { return f2d_exact(v); }
+template <>
+__device__ __forceinline__ double tod<double>(double v) { return v; }
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// partial[b] = sum over the block's grid-stride share of a[i]*b[i]
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ a, const T* __restrict__ b,
+                                                     long long n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s = fma(tod(a[i]), tod(b[i]), s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[0] = sum partial (fixed order); if sqrt_it, out = sqrt(out)
+__global__ void k_finish(const double* __restrict__ partial, int n, double* __restrict__ out, int sqrt_it) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[0] = sqrt_it ? sqrt(s) : s;
+}
+
+// w -= a[0] * v + (bprev ? bprev[0] : 0) * vp
+template <class T>
+__global__ void k_axpy2(T* __restrict__ w, const T* __restrict__ v, const T* __restrict__ vp,
+                        const double* __restrict__ a, const double* __restrict__ bprev, long long n) {
+  const double al = a[0];
+  const double be = bprev ? bprev[0] : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double r = tod(w[i]) - al * tod(v[i]);
+    if (vp) r -= be * tod(vp[i]);
+    w[i] = (T)r;
+  }
+}
+
+// v = w / b[0] (zero vector if b[0] is below tol: breakdown)
+template <class T>
+__global__ void k_scale(T* __restrict__ v, const T* __restrict__ w, const double* __restrict__ b,
+                        double tol, long long n) {
+  const double bb = b[0];
+  const double inv = (bb > tol) ? 1.0 / bb : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = (T)(tod(w[i]) * inv);
+}
+
+// psi += coef * v
+template <class T>
+__global__ void k_axpy(T* __restrict__ psi, const T* __restrict__ v, double coef, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    psi[i] = (T)(tod(psi[i]) + coef * tod(v[i]));
+}
+
+template <class T>
+__global__ void k_copy_scaled(T* __restrict__ dst, const T* __restrict__ src, double scale, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (T)(tod(src[i]) * scale);
+}
+
+// ---------------------------------------------------------------------------
+// host tridiagonal eigensolver
+// ---------------------------------------------------------------------------
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double lam) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double bb = (i == 0) ? 0.0 : b[i - 1] * b[i - 1];
+    q = (a[i] - lam) - ((i == 0) ? 0.0 : bb / q);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+static double lowest_eigenvalue(const std::vector<double>& a, const std::vector<double>& b) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < a.size(); ++i) {  // Gershgorin interval
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (sturm_count(a, b, mid) >= 1) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Solve (T - lam I) u = rhs with Gaussian elimination and partial pivoting on
+// the tridiagonal band (one extra superdiagonal appears from row swaps).
+static void tri_solve(const std::vector<double>& a, const std::vector<double>& b, double lam,
+                      std::vector<double>& u) {
+  const int n = (int)a.size();
+  std::vector<double> d(n), du(n, 0.0), du2(n, 0.0), dl(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = a[i] - lam;
+  for (int i = 0; i + 1 < n; ++i) { du[i] = b[i]; dl[i] = b[i]; }
+  std::vector<double> r = u;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (std::fabs(d[i]) >= std::fabs(dl[i])) {
+      double piv = (d[i] == 0.0) ? 1e-300 : d[i];
+      double f = dl[i] / piv;
+      d[i + 1] -= f * du[i];
+      if (i + 2 < n) du[i + 1] -= f * du2[i];
+      r[i + 1] -= f * r[i];
+    } else {
+      double f = d[i] / dl[i];
+      // swap rows i and i+1
+      double t0 = d[i], t1 = du[i];
+      d[i] = dl[i];
+      du[i] = d[i + 1];
+      du2[i] = (i + 2 < n) ? du[i + 1] : 0.0;
+      d[i + 1] = t1 - f * du[i];
+      if (i + 2 < n) du[i + 1] = -f * du2[i];
+      (void)t0;
+      std::swap(r[i], r[i + 1]);
+      r[i + 1] -= f * r[i];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = r[i];
+    if (i + 1 < n) s -= du[i] * r[i + 1];
+    if (i + 2 < n) s -= du2[i] * r[i + 2];
+    double piv = (d[i] == 0.0) ? 1e-300 : d[i];
+    r[i] = s / piv;
+  }
+  u.swap(r);
+}
+
+static std::vector<double> lowest_eigvec(const std::vector<double>& a, const std::vector<double>& b,
+                                         double lam) {
+  const int n = (int)a.size();
+  std::vector<double> u(n, 1.0);
+  double scale = 1.0;
+  for (size_t i = 0; i < a.size(); ++i) scale = std::max(scale, std::fabs(a[i]));
+  const double shift = lam - 1e-13 * scale;
+  for (int it = 0; it < 4; ++it) {
+    tri_solve(a, b, shift, u);
+    double nrm = 0.0;
+    for (double v : u) nrm += v * v;
+    nrm = std::sqrt(nrm);
+    for (double& v : u) v /= nrm;
+  }
+  return u;
+}
+
+// ---------------------------------------------------------------------------
+// driver
+// ---------------------------------------------------------------------------
+template <class T>
+static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, double* alpha,
+                     double* beta, int* steps_done, T* psi0, double* e0, cudaStream_t s) {
+  const long long n = p->D;
+  const int vb = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+  const int rb = (int)std::min<long long>((n + kRedThreads - 1) / kRedThreads, kRedBlocks);
+  T *V = nullptr;
+  double* dsc = nullptr;  // [rb partials][alpha steps][beta steps][tmp 4]
+  cudaError_t e = cudaMalloc(&V, sizeof(T) * n * 3);
+  if (e != cudaSuccess) return cuda_fail(e, "Lanczos work vectors");
+  e = cudaMalloc(&dsc, sizeof(double) * (rb + 2 * (size_t)steps + 8));
+  if (e != cudaSuccess) {
+    cudaFree(V);
+    return cuda_fail(e, "Lanczos scalars");
+  }
+  T* vk = V;
+  T* vp = V + n;
+  T* w = V + 2 * n;
+  double* part = dsc;
+  double* dal = dsc + rb;
+  double* dbe = dal + steps;
+  double* tmp = dbe + steps;
+  int rc = HM_OK;
+
+  auto dot = [&](const T* a, const T* b, double* out, int sq) {
+    k_dot<T><<<rb, kRedThreads, 0, s>>>(a, b, n, part);
+    k_finish<<<1, 256, 0, s>>>(part, rb, out, sq);
+  };
+  // one pass of the recurrence; if psi != nullptr, also psi += u[k] v_k
+  auto run = [&](int m, const std::vector<double>* u, T* psi) -> int {
+    dot(v0, v0, tmp, 1);
+    k_scale<T><<<vb, 256, 0, s>>>(vk, v0, tmp, 0.0, n);
+    cudaMemsetAsync(vp, 0, sizeof(T) * n, s);
+    for (int k = 0; k < m; ++k) {
+      if (psi) k_axpy<T><<<vb, 256, 0, s>>>(psi, vk, (*u)[k], n);
+      auto it = p->tuned.find({(int)dt, 1LL});
+      cudaError_t le = apply_kplan(p->k, vk, w, 1, dt, s, it == p->tuned.end() ? 0 : it->second, false);
+      if (le != cudaSuccess) return cuda_fail(le, "Lanczos apply");
+      dot(vk, w, dal + k, 0);
+      k_axpy2<T><<<vb, 256, 0, s>>>(w, vk, k > 0 ? vp : nullptr, dal + k, k > 0 ? dbe + k - 1 : nullptr, n);
+      if (flags & 1) {  // local reorthogonalisation (second Gram-Schmidt pass)
+        dot(vk, w, tmp + 1, 0);
+        if (k > 0) dot(vp, w, tmp + 2, 0);
+        k_axpy2<T><<<vb, 256, 0, s>>>(w, vk, k > 0 ? vp : nullptr, tmp + 1, k > 0 ? tmp + 2 : nullptr, n);
+      }
+      if (k == m - 1) break;
+      dot(w, w, dbe + k, 1);
+      std::swap(vp, vk);                         // v_{k-1} <- v_k
+      k_scale<T><<<vb, 256, 0, s>>>(vk, w, dbe + k, 0.0, n);  // v_{k+1} = w / beta_k
+    }
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return cuda_fail(le, "Lanczos kernels");
+    return HM_OK;
+  };
+
+  rc = run(steps, nullptr, nullptr);
+  if (rc == HM_OK) {
+    std::vector<double> ha(steps), hb(steps, 0.0);
+    e = cudaMemcpyAsync(ha.data(), dal, sizeof(double) * steps, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && steps > 1)
+      e = cudaMemcpyAsync(hb.data(), dbe, sizeof(double) * (steps - 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "Lanczos scalars to host");
+    if (rc == HM_OK) {
+      double amax = 0.0;
+      for (double v : ha) amax = std::max(amax, std::fabs(v));
+      int m = steps;
+      for (int k = 0; k + 1 < steps; ++k)
+        if (!(hb[k] > 1e-14 * std::max(1.0, amax))) {  // breakdown (also catches NaN)
+          m = k + 1;
+          rc = HM_LANCZOS_BREAKDOWN;
+          break;
+        }
+      std::vector<double> a(ha.begin(), ha.begin() + m), b(hb.begin(), hb.begin() + std::max(0, m - 1));
+      for (int k = 0; k < steps; ++k) {
+        alpha[k] = k < m ? ha[k] : 0.0;
+        beta[k] = k + 1 < m ? hb[k] : 0.0;
+      }
+      *steps_done = m;
+      *e0 = lowest_eigenvalue(a, b);
+      if (psi0) {
+        std::vector<double> u = lowest_eigvec(a, b, *e0);
+        cudaMemsetAsync(psi0, 0, sizeof(T) * n, s);
+        int rc2 = run(m, &u, psi0);
+        if (rc2 != HM_OK) rc = rc2;
+        else {
+          dot(psi0, psi0, tmp + 3, 1);
+          double nrm = 0.0;
+          e = cudaMemcpyAsync(&nrm, tmp + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+          if (e == cudaSuccess && nrm > 0.0) {
+            k_copy_scaled<T><<<vb, 256, 0, s>>>(psi0, psi0, 1.0 / nrm, n);
+            e = cudaStreamSynchronize(s);
+          }
+          if (e != cudaSuccess) rc = cuda_fail(e, "Ritz vector");
+        }
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(V);
+  cudaFree(dsc);
+  return rc;
+}
+
+int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,
+                double* beta, int* steps_done, void* psi0, double* e0, cudaStream_t s) {
+  if (dt == HM_F32)
+    return lanczos_t<float>(p, (const float*)v0, steps, dt, flags, alpha, beta, steps_done,
+                            (float*)psi0, e0, s);
+  return lanczos_t<double>(p, (const double*)v0, steps, dt, flags, alpha, beta, steps_done,
+                           (double*)psi0, e0, s);
+}
+
+}  // namespace hm

@@ -1,0 +1,189 @@
+"""Python front end of the hm C ABI. Argument marshalling only: every step of
+the Hamiltonian action runs in the CUDA library; torch supplies device memory
+and streams."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _capi as C
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return C.HM_F64
+    if t.dtype == torch.float32:
+        return C.HM_F32
+    raise TypeError(f"vectors must be float64 or float32, got {t.dtype}")
+
+
+def _check_vec(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _site_kind(k):
+    if k in ("spin", C.HM_SPIN):
+        return C.HM_SPIN
+    if k in ("boson", C.HM_BOSON):
+        return C.HM_BOSON
+    raise ValueError(f"unknown site kind {k!r}")
+
+
+def _op(o):
+    return C.OPS[o] if isinstance(o, str) else int(o)
+
+
+class Hamiltonian:
+    """H = sum_t coef_t op_i(t) op_j(t) on sites [(kind, dim), ...].
+
+    terms: iterable of (i, op_i, j, op_j, coef), j = -1 for single-site terms;
+    op names as in include/hm.h ("Sz", "Sx", "Sy", "Sp", "Sm", "Sz2", "Sp2",
+    "Sm2", "N", "a", "adag", "I")."""
+
+    def __init__(self, sites, terms):
+        self._lib = C.load()
+        torch.cuda.init()
+        self.sites = [(_site_kind(k), int(d)) for k, d in sites]
+        self.terms = [(int(i), _op(oi), int(j), _op(oj), float(c)) for i, oi, j, oj, c in terms]
+        cs = (C.hm_site * len(self.sites))(*[C.hm_site(k, d) for k, d in self.sites])
+        ts = (C.hm_term * max(1, len(self.terms)))(*[C.hm_term(i, oi, j, oj, c) for i, oi, j, oj, c in self.terms])
+        h = ctypes.c_void_p()
+        C.check(self._lib.hm_create(cs, len(self.sites), ts, len(self.terms), ctypes.byref(h)), "hm_create")
+        self._h = h
+        self.D = int(self._lib.hm_dim(h))
+        self.nterms = len(self.terms)
+        self.coefs = [t[4] for t in self.terms]
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.hm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- coefficients ------------------------------------------------------
+    def set_coefficients(self, coefs):
+        c = [float(v) for v in (coefs.detach().cpu().tolist() if torch.is_tensor(coefs) else coefs)]
+        if len(c) != self.nterms:
+            raise ValueError(f"expected {self.nterms} coefficients, got {len(c)}")
+        arr = (ctypes.c_double * max(1, self.nterms))(*c)
+        C.check(self._lib.hm_set_coefficients(self._h, arr), "hm_set_coefficients")
+        self.coefs = c
+
+    # -- y = H x -------------------------------------------------------------
+    def _nvec(self, x):
+        if x.numel() % self.D:
+            raise ValueError(f"vector length {x.numel()} is not a multiple of D={self.D}")
+        return x.numel() // self.D
+
+    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """y = H x for x of D*nvec elements (state-major, x[k*nvec + v])."""
+        _check_vec(x, "x")
+        y = torch.empty_like(x) if out is None else out
+        _check_vec(y, "out")
+        C.check(self._lib.hm_apply(self._h, x.data_ptr(), y.data_ptr(), self._nvec(x), _dtype_code(x),
+                                   _stream(stream)), "hm_apply")
+        return y
+
+    def apply_ex(self, x, out=None, native_f64=False, transpose=False, ctas=0, stream=None):
+        _check_vec(x, "x")
+        y = torch.empty_like(x) if out is None else out
+        flags = (1 if native_f64 else 0) | (2 if transpose else 0)
+        C.check(self._lib.hm_apply_ex(self._h, x.data_ptr(), y.data_ptr(), self._nvec(x), _dtype_code(x),
+                                      flags, int(ctas), _stream(stream)), "hm_apply_ex")
+        return y
+
+    def adjoint(self, gy, x=None, want_gx=True, want_gcoef=True, gx=None, gcoef=None, stream=None):
+        """gx = H^T gy and gcoef[t] = sum_v <gy_v|O_t|x_v> (float64, device)."""
+        _check_vec(gy, "gy")
+        if want_gx and gx is None:
+            gx = torch.empty_like(gy)
+        if want_gcoef and gcoef is None:
+            gcoef = torch.empty(max(1, self.nterms), dtype=torch.float64, device=gy.device)
+        if want_gcoef:
+            if x is None:
+                raise ValueError("x is needed for coupling gradients")
+            _check_vec(x, "x")
+        C.check(self._lib.hm_apply_adjoint(
+            self._h, gy.data_ptr(), x.data_ptr() if x is not None else None,
+            gx.data_ptr() if want_gx else None, gcoef.data_ptr() if want_gcoef else None,
+            self._nvec(gy), _dtype_code(gy), _stream(stream)), "hm_apply_adjoint")
+        return (gx if want_gx else None), (gcoef[: self.nterms] if want_gcoef else None)
+
+    def lanczos(self, v0: torch.Tensor, steps: int, reorth: bool = False, ritz_vector: bool = False,
+                stream=None):
+        """Ground state by device Lanczos; returns dict(e0, alpha, beta, steps, psi0, breakdown)."""
+        _check_vec(v0, "v0")
+        if v0.numel() != self.D:
+            raise ValueError("v0 must have D elements")
+        a = (ctypes.c_double * steps)()
+        b = (ctypes.c_double * steps)()
+        done = ctypes.c_int32(0)
+        e0 = ctypes.c_double(0.0)
+        psi = torch.empty_like(v0) if ritz_vector else None
+        rc = self._lib.hm_lanczos(self._h, v0.data_ptr(), steps, _dtype_code(v0), 1 if reorth else 0, a, b,
+                                  ctypes.byref(done), psi.data_ptr() if psi is not None else None,
+                                  ctypes.byref(e0), _stream(stream))
+        C.check(rc, "hm_lanczos")
+        m = done.value
+        return {"e0": e0.value, "alpha": list(a)[:m], "beta": list(b)[: max(0, m - 1)], "steps": m,
+                "psi0": psi, "breakdown": rc == C.HM_LANCZOS_BREAKDOWN}
+
+    def tune(self, nvec: int = 1, dtype=torch.float64, stream=None):
+        code = C.HM_F64 if dtype == torch.float64 else C.HM_F32
+        C.check(self._lib.hm_tune(self._h, int(nvec), code, _stream(stream)), "hm_tune")
+
+
+class Batch:
+    """Many Hamiltonians applied in one persistent launch (uneven sizes)."""
+
+    def __init__(self, hams):
+        self._lib = C.load()
+        self.hams = list(hams)
+        arr = (ctypes.c_void_p * len(self.hams))(*[h.handle.value for h in self.hams])
+        b = ctypes.c_void_p()
+        C.check(self._lib.hm_batch_create(arr, len(self.hams), ctypes.byref(b)), "hm_batch_create")
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._lib.hm_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, xs, ys=None, stream=None):
+        if len(xs) != len(self.hams):
+            raise ValueError("one x per Hamiltonian")
+        ys = [torch.empty_like(x) for x in xs] if ys is None else ys
+        for x, y in zip(xs, ys):
+            _check_vec(x, "x")
+            _check_vec(y, "y")
+        nvec = xs[0].numel() // self.hams[0].D
+        xp = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        yp = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        C.check(self._lib.hm_batch_apply(self._b, xp, yp, nvec, _dtype_code(xs[0]), _stream(stream)),
+                "hm_batch_apply")
+        return ys
