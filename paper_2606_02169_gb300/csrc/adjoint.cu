@@ -13,8 +13,6 @@
 
 namespace hm {
 
-cudaError_t apply_kplan(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt,
-                        cudaStream_t s, int ctas, bool native_f64);
 
 template <class T>
 __device__ __forceinline__ double as_f64(T v);
@@ -151,8 +149,8 @@ int launch_term_grad(const Plan* p, const void* gy, const void* x, double* gcoef
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef, long long nvec,
                    hm_dtype dt, cudaStream_t s) {
   if (gx) {
-    cudaError_t e = apply_kplan(p->kt, gy, gx, nvec, dt, s, 0, false);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint apply launch");
+    int rc = apply_on(p, p->kt, gy, gx, nvec, dt, s, 0, false);
+    if (rc) return rc;
   }
   if (!gcoef) return HM_OK;
   const int nterms = (int)p->terms.size();

@@ -1,11 +1,11 @@
-// Host entry points of the apply path: dtype dispatch, device properties and
-// the batched launch. The kernels live in apply_kernel.cuh and are
-// instantiated per arithmetic policy in apply_f32.cu / apply_df64.cu /
-// apply_f64.cu.
+// Host entry points of the apply path: dtype dispatch, the FP64 split pass,
+// device properties and the batched launch. The kernels live in
+// apply_kernel.cuh and are instantiated per arithmetic policy in
+// apply_f32.cu / apply_df64.cu / apply_f64.cu.
 #include <algorithm>
 #include <vector>
 
-#include "device_common.cuh"
+#include "apply_kernel.cuh"
 
 namespace hm {
 
@@ -26,18 +26,82 @@ int num_sms() {
   return g_nsm;
 }
 
-cudaError_t apply_kplan(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
-                        int ctas, bool native_f64) {
-  if (dt == HM_F32) return launch_apply_t<AR_F32>(k, x, y, nvec, s, ctas);
-  if (native_f64) return launch_apply_t<AR_F64>(k, x, y, nvec, s, ctas);
-  return launch_apply_t<AR_DF64>(k, x, y, nvec, s, ctas);
+// FP64 input split into (hi, lo) float pairs: 16-byte loads and stores when
+// x is 16-byte aligned (the output buffer always is)
+__global__ void __launch_bounds__(256) k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n) {
+  const long long n2 = n >> 1;
+  const double2* __restrict__ x2 = reinterpret_cast<const double2*>(x);
+  float4* __restrict__ xs4 = reinterpret_cast<float4*>(xs);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = __ldcs(x2 + i);
+    const float2 a = split_f64(v.x), b = split_f64(v.y);
+    xs4[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) xs[n - 1] = split_f64(x[n - 1]);
 }
 
-int launch_apply(const Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
-                 int ctas_override) {
-  cudaError_t e = apply_kplan(p->k, x, y, nvec, dt, s, ctas_override, false);
+// element-wise variant for an x that is only 8-byte aligned
+__global__ void __launch_bounds__(256) k_split_f64_scalar(const double* __restrict__ x, float2* __restrict__ xs, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    xs[i] = split_f64(__ldcs(x + i));
+}
+
+// Plan-owned buffer for the split input, grown on demand (stream-ordered:
+// the previous users of the old buffer on `s` finish before it is freed).
+static void* split_buffer(Plan* p, size_t bytes, cudaStream_t s, int* rc) {
+  if (p->xsplit_bytes >= bytes) return p->xsplit;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone) {
+    set_error("FP64 apply needs its split buffer grown: run it once before stream capture");
+    *rc = HM_ERR_INVALID_ARG;
+    return nullptr;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && p->xsplit) e = cudaFree(p->xsplit);
+  p->xsplit = nullptr;
+  p->xsplit_bytes = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&p->xsplit, bytes);
+  if (e != cudaSuccess) {
+    p->xsplit = nullptr;
+    *rc = cuda_fail(e, "FP64 split buffer");
+    return nullptr;
+  }
+  p->xsplit_bytes = bytes;
+  return p->xsplit;
+}
+
+cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
+  const long long grid = std::max<long long>(1, std::min<long long>((n / 2 + 255) / 256, (long long)num_sms() * 8));
+  if (((uintptr_t)x % 16) == 0 && ((uintptr_t)xs % 16) == 0)
+    k_split_f64<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n);
+  else
+    k_split_f64_scalar<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n);
+  return cudaGetLastError();
+}
+
+// y = H x (or H^T x for the transposed KPlan) on stream s
+int apply_on(Plan* p, const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+             int ctas, bool native_f64) {
+  cudaError_t e;
+  if (dt == HM_F32) {
+    e = launch_apply_t<AR_F32>(k, x, y, nvec, s, ctas);
+  } else if (native_f64) {
+    e = launch_apply_t<AR_F64>(k, x, y, nvec, s, ctas);
+  } else {
+    int rc = HM_OK;
+    const long long n = p->D * nvec;
+    void* xs = split_buffer(p, (size_t)n * sizeof(float2), s, &rc);
+    if (!xs) return rc;
+    e = split_into(x, xs, n, s);
+    if (e == cudaSuccess) e = launch_apply_t<AR_DF64>(k, xs, y, nvec, s, ctas);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   return HM_OK;
+}
+
+int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, int ctas) {
+  return apply_on(p, p->k, x, y, nvec, dt, s, ctas, false);
 }
 
 int batch_setup(Plan* b) {
@@ -74,8 +138,23 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
     if (rc) return rc;
   }
   std::vector<const Plan*> mem(b->members.begin(), b->members.end());
-  cudaError_t e = (dt == HM_F32) ? launch_batch_t<AR_F32>((const KPlan*)b->batch_dev, mem, xs, ys, nvec, s)
-                                 : launch_batch_t<AR_DF64>((const KPlan*)b->batch_dev, mem, xs, ys, nvec, s);
+  cudaError_t e;
+  if (dt == HM_F32) {
+    e = launch_batch_t<AR_F32>((const KPlan*)b->batch_dev, mem, xs, ys, nvec, s);
+  } else {
+    // each member's FP64 input is split into that member's buffer first
+    std::vector<const void*> sx(mem.size());
+    for (size_t i = 0; i < mem.size(); ++i) {
+      int rc = HM_OK;
+      Plan* p = b->members[i];
+      void* buf = split_buffer(p, (size_t)(p->D * nvec) * sizeof(float2), s, &rc);
+      if (!buf) return rc;
+      e = split_into(xs[i], buf, p->D * nvec, s);
+      if (e != cudaSuccess) return cuda_fail(e, "batch split");
+      sx[i] = buf;
+    }
+    e = launch_batch_t<AR_DF64>((const KPlan*)b->batch_dev, mem, sx.data(), ys, nvec, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return HM_OK;
 }

@@ -9,17 +9,20 @@
 //   * the high digits (Eq. decode on the block index);
 //   * every channel on high digits only (Sec. IV.B steps 2-4: admissibility
 //     and coefficient are uniform over the block);
-//   * the high factor u of every factorised high/low channel.
+//   * the high factor u of every factorised high/low channel, and whether
+//     the member's source range of this block lies inside the vector.
 // Per element the thread then does one load and one FMA per active uniform
-// hop, a low-digit lookup per factorised group, and reads the channels inside
-// the low block (the same small operator for every block) from an ELL table.
-// Thread t owns elements t, t+NT, ..., t+(S-1)NT of each chunk, so each hop
-// is S independent coalesced loads with immediate offsets.
+// hop, a low-digit lookup per factorised group, and one packed ELL entry per
+// hop inside the low block (the same small operator for every block).
+// Thread t owns elements t, t+NT, ..., t+(S-1)NT of a chunk, so each hop is S
+// independent coalesced loads with immediate offsets.
 #pragma once
 
 #include "device_common.cuh"
 
 namespace hm {
+
+constexpr int kNT = 256;  // threads per CTA of the apply kernels
 
 template <int AR>
 struct Lists {  // per-block uniform values (shared memory)
@@ -28,7 +31,12 @@ struct Lists {  // per-block uniform values (shared memory)
   int* hd;              // [64] high digits
   C* hh_c;              // [n_hh_diag + n_hh] coefficient of each high channel
   long long* hh_src;    // [n_hh_diag + n_hh] element index of its source block
-  C* mem_u;             // [n_mem]
+  int* n_act;           // [1] number of active off-diagonal high channels
+  C* act_c;             // [n_hh] their coefficients, in channel order
+  long long* act_src;   // [n_hh] their source-block element index
+  C* mem_u;             // [n_mem] high factor u of each group member
+  long long* mem_src;   // [n_mem] element offset of each member's source
+  int* mem_ok;          // [n_mem] source range of this block inside the vector
   int* grp_v;           // [n_grp_diag + n_grp] v row base
   Dsum* grp_U;          // [n_grp_diag] sum of member u (diagonal groups)
   Dsum* du;             // [1] sum of high diagonal channels
@@ -39,8 +47,8 @@ __host__ __device__ inline size_t lists_bytes(int n_hh, int n_mem, int n_grp, in
   using C = typename Ar<AR>::C;
   using Dsum = typename Ar<AR>::Dsum;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return al(64 * 4) + al(n_hh * sizeof(C)) + al(n_hh * 8) + al(n_mem * sizeof(C)) + al(n_grp * 4) +
-         al(n_grpd * sizeof(Dsum)) + al(sizeof(Dsum));
+  return al(64 * 4) + 2 * al(n_hh * sizeof(C)) + 2 * al(n_hh * 8) + al(16) + al(n_mem * sizeof(C)) + al(n_mem * 8) +
+         al(n_mem * 4) + al(n_grp * 4) + al(n_grpd * sizeof(Dsum)) + al(sizeof(Dsum));
 }
 
 template <int AR>
@@ -56,8 +64,18 @@ __device__ inline Lists<AR> carve(unsigned char* sm, int n_hh, int n_mem, int n_
   o += al(n_hh * sizeof(C));
   L.hh_src = (long long*)(sm + o);
   o += al(n_hh * 8);
+  L.n_act = (int*)(sm + o);
+  o += al(16);
+  L.act_c = (C*)(sm + o);
+  o += al(n_hh * sizeof(C));
+  L.act_src = (long long*)(sm + o);
+  o += al(n_hh * 8);
   L.mem_u = (C*)(sm + o);
   o += al(n_mem * sizeof(C));
+  L.mem_src = (long long*)(sm + o);
+  o += al(n_mem * 8);
+  L.mem_ok = (int*)(sm + o);
+  o += al(n_mem * 4);
   L.grp_v = (int*)(sm + o);
   o += al(n_grp * 4);
   L.grp_U = (Dsum*)(sm + o);
@@ -66,10 +84,10 @@ __device__ inline Lists<AR> carve(unsigned char* sm, int n_hh, int n_mem, int n_
   return L;
 }
 
-// Evaluate the uniform values of low block `blk`. Must be called by all
-// threads of the CTA; ends with a barrier.
+// Evaluate the uniform values of low block `blk`. Called by all threads of
+// the CTA; ends with a barrier.
 template <int AR>
-__device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, long long blk, long long nvec) {
+__device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, long long blk, int nvec) {
   using A = Ar<AR>;
   using C = typename A::C;
   using Dsum = typename A::Dsum;
@@ -83,11 +101,14 @@ __device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, l
     const int ni = L.hd[ch.si];
     const int nj = (ch.kind & CK_SINGLE) ? 0 : L.hd[ch.sj];
     L.hh_c[c] = tab[ch.tab + ni * ch.dj + nj];
-    L.hh_src[c] = (blk * P.B + ch.off) * nvec;
+    L.hh_src[c] = (blk * P.B + ch.off) * (long long)nvec;
   }
+  const long long b0 = blk * P.B;
   for (int m = threadIdx.x; m < P.n_mem; m += nt) {
     const KMember mb = P.mem[m];
     L.mem_u[m] = tab[mb.utab + L.hd[mb.usite]];
+    L.mem_src[m] = mb.off * (long long)nvec;
+    L.mem_ok[m] = (b0 + mb.off >= 0) && (b0 + mb.off + P.B <= P.D);
   }
   const int ng = P.n_grp_diag + P.n_grp;
   for (int g = threadIdx.x; g < ng; g += nt) {
@@ -95,11 +116,20 @@ __device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, l
     L.grp_v[g] = gr.vtab + (gr.vstride ? L.hd[gr.vsite] * gr.vstride : 0);
   }
   __syncthreads();
-  // fixed-order sums (deterministic)
+  // fixed-order sums and the compacted active list (deterministic)
   if (threadIdx.x == 0) {
     Dsum d = A::dzero();
     for (int c = 0; c < P.n_hh_diag; ++c) A::dadd(d, L.hh_c[c]);
     L.du[0] = d;
+  } else if (threadIdx.x == 32) {
+    int n = 0;
+    for (int c = P.n_hh_diag; c < nhh; ++c)
+      if (A::nz(L.hh_c[c])) {
+        L.act_c[n] = L.hh_c[c];
+        L.act_src[n] = L.hh_src[c];
+        ++n;
+      }
+    L.n_act[0] = n;
   }
   for (int g = threadIdx.x; g < P.n_grp_diag; g += nt) {
     const KGroup gr = P.grp[g];
@@ -119,22 +149,28 @@ struct NvDiv {
   }
 };
 
-// One chunk of NT*S elements of low block blk (uniforms already in L).
-template <int AR, int NT, int S>
+// One chunk of NT*S elements starting at element `e_start` of low block blk
+// (uniforms already in L). FULL: every element of the chunk lies inside the
+// block, so no per-element bounds predicates are needed. NV1: nvec == 1.
+template <int AR, int S, bool FULL, bool NV1>
 __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
-                                            const typename Ar<AR>::T* __restrict__ x,
-                                            typename Ar<AR>::T* __restrict__ y, long long nvec,
-                                            NvDiv nvdiv, long long blk, int chunk) {
+                                            const typename Ar<AR>::TX* __restrict__ x,
+                                            typename Ar<AR>::TY* __restrict__ y, int nvec_rt, NvDiv nvdiv,
+                                            long long blk, int e_start) {
   using A = Ar<AR>;
-  using T = typename A::T;
+  using TX = typename A::TX;
+  using TY = typename A::TY;
   using C = typename A::C;
   using Acc = typename A::Acc;
   using Dsum = typename A::Dsum;
+  using E = typename A::E;
+  constexpr int NT = kNT;
+  const int nvec = NV1 ? 1 : nvec_rt;
   const C* __restrict__ tab = A::tab(P);
-  const int belems = (int)(P.B * nvec);
+  const int belems = P.B * nvec;
   const long long ebase = blk * (long long)belems;
-  const int e0 = chunk * (NT * S) + (int)threadIdx.x;
-  const T* __restrict__ xb = x + ebase + e0;  // own element s at xb[s*NT]
+  const int e0 = e_start + (int)threadIdx.x;
+  const TX* __restrict__ xb = x + ebase + e0;  // own element s at xb[s*NT]
 
   bool ok[S];
   int lo[S];
@@ -142,8 +178,8 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int e = e0 + s * NT;
-    ok[s] = e < belems;
-    lo[s] = ok[s] ? nvdiv(e) : 0;
+    ok[s] = FULL || e < belems;
+    lo[s] = ok[s] ? (NV1 ? e : nvdiv(e)) : 0;
     pk[s] = __ldg(P.ptab + lo[s]);
   }
 
@@ -167,78 +203,124 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      const T xv = ok[s] ? xb[s * NT] : T(0);
-      acc[s] = A::dmul(ds[s], A::prep(xv));
+      TX xv;
+      if (FULL || ok[s]) xv = __ldg(xb + s * NT);
+      else xv = TX{};
+      acc[s] = A::dmul(ds[s], xv);
     }
   }
-  // ---- hops with block-uniform coefficients (high digits only) ----
-  const int nhh = P.n_hh_diag + P.n_hh;
-  for (int c = P.n_hh_diag; c < nhh; ++c) {
-    const C cf = L.hh_c[c];
-    if (!A::nz(cf)) continue;  // a source digit leaves its range (Sec. IV.B step 3)
-    const T* __restrict__ src = x + L.hh_src[c] + e0;
+  // ---- hops with block-uniform coefficients (high digits only); the list
+  //      holds only channels whose source digits are in range (Sec. IV.B step 3) ----
+  const int nact = L.n_act[0];
+#pragma unroll(S >= 6 ? 2 : 4)
+  for (int c = 0; c < nact; ++c) {
+    const C cf = L.act_c[c];
+    const TX* __restrict__ src = x + L.act_src[c] + e0;
 #pragma unroll
     for (int s = 0; s < S; ++s)
-      if (ok[s]) A::fma(acc[s], cf, A::prep(__ldg(src + s * NT)));
+      if (FULL || ok[s]) A::fma(acc[s], cf, __ldg(src + s * NT));
   }
   // ---- factorised high/low hops, grouped by their low factor ----
   for (int g = P.n_grp_diag; g < P.n_grp_diag + P.n_grp; ++g) {
     const KGroup gr = P.grp[g];
     const int vb = L.grp_v[g];
     C v[S];
-    bool pr[S];
     Acc ag[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       v[s] = tab[vb + low_digit(pk[s], gr.lbit, gr.lwid)];
-      pr[s] = ok[s] && A::nz(v[s]);
       ag[s] = A::azero();
     }
+#pragma unroll(S >= 6 ? 2 : 4)
     for (int m = gr.m0; m < gr.m1; ++m) {
       const C u = L.mem_u[m];
       if (!A::nz(u)) continue;
-      const T* __restrict__ src = xb + P.mem[m].off * nvec;
+      const TX* __restrict__ src = xb + L.mem_src[m];
+      if (L.mem_ok[m]) {
+        // every address of this member lies inside x: an inadmissible low
+        // digit (v = 0) gathers a finite in-range value that is then scaled
+        // by exactly zero
 #pragma unroll
-      for (int s = 0; s < S; ++s)
-        if (pr[s]) A::fma(ag[s], u, A::prep(__ldg(src + s * NT)));
+        for (int s = 0; s < S; ++s)
+          if (FULL || ok[s]) A::fma(ag[s], u, __ldg(src + s * NT));
+      } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          if ((FULL || ok[s]) && A::nz(v[s])) A::fma(ag[s], u, __ldg(src + s * NT));
+      }
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) A::acc_mul(acc[s], v[s], ag[s]);
   }
-  // ---- hops inside the low block (ELL over the low index) ----
+  // ---- hops inside the low block: packed ELL {delta, coef}, zero padding ----
   {
-    const C* __restrict__ etab = A::ell(P);
+    const E* __restrict__ et = A::ell(P);
+#pragma unroll(S >= 6 ? 2 : 4)
     for (int w = 0; w < P.ell_w; ++w) {
-      const long long rb = (long long)w * P.B;
+      const E* __restrict__ er = et + (long long)w * P.B;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const C cf = etab[rb + lo[s]];
-        const int dl = __ldg(P.ell_delta + rb + lo[s]);
-        if (ok[s] && A::nz(cf)) A::fma(acc[s], cf, A::prep(__ldg(xb + s * NT + (long long)dl * nvec)));
+        const E en = __ldg(er + lo[s]);
+        if (FULL || ok[s])
+          A::fma(acc[s], A::ell_coef(en), __ldg(xb + (s * NT + A::ell_delta(en) * nvec)));
       }
     }
   }
   // ---- store: one write per output element ----
-  T* __restrict__ yb = y + ebase + e0;
+  TY* __restrict__ yb = y + ebase + e0;
 #pragma unroll
   for (int s = 0; s < S; ++s)
-    if (ok[s]) yb[s * NT] = A::out(acc[s]);
+    if (FULL || ok[s]) yb[s * NT] = A::out(acc[s]);
 }
 
-template <int AR, int NT, int S>
-__global__ void __launch_bounds__(NT)
-k_apply(const KPlan P, const typename Ar<AR>::T* __restrict__ x, typename Ar<AR>::T* __restrict__ y,
-        long long nvec, NvDiv nvdiv, int nchunks) {
+// A block of belems elements is cut into nS chunks of NT*S elements, then n1
+// chunks of NT elements, then (if needed) one partial NT-chunk, so all but
+// the last chunk run without per-element predicates.
+struct ChunkPlan {
+  int nS, n1, tail;  // tail: 1 if a partial chunk follows
+  __host__ __device__ int count() const { return nS + n1 + tail; }
+};
+
+__host__ __device__ inline ChunkPlan chunk_plan(int belems, int S) {
+  ChunkPlan c;
+  c.nS = belems / (kNT * S);
+  const int rem = belems - c.nS * kNT * S;
+  c.n1 = rem / kNT;
+  c.tail = (rem - c.n1 * kNT) > 0;
+  return c;
+}
+
+template <int AR, int S, bool NV1>
+__device__ __forceinline__ void apply_item(const KPlan& P, const Lists<AR>& L, const typename Ar<AR>::TX* x,
+                                           typename Ar<AR>::TY* y, int nvec, NvDiv nvdiv, long long blk,
+                                           const ChunkPlan& cp, int c) {
+  if (c < cp.nS) {
+    apply_chunk<AR, S, true, NV1>(P, L, x, y, nvec, nvdiv, blk, c * kNT * S);
+  } else if (c < cp.nS + cp.n1) {
+    apply_chunk<AR, 1, true, NV1>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + (c - cp.nS) * kNT);
+  } else {
+    apply_chunk<AR, 1, false, NV1>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + cp.n1 * kNT);
+  }
+}
+
+template <int AR> struct MinBlocks { static constexpr int v = 2; };
+template <> struct MinBlocks<AR_F32> { static constexpr int v = 4; };
+
+template <int AR, int S, bool NV1>
+__global__ void __launch_bounds__(kNT, MinBlocks<AR>::v)
+k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>::TY* __restrict__ y,
+        int nvec, NvDiv nvdiv) {
   extern __shared__ __align__(16) unsigned char sm[];
   const Lists<AR> L = carve<AR>(sm, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
+  const ChunkPlan cp = chunk_plan(P.B * nvec, S);
+  const int nchunks = cp.count();
   const long long nitems = P.nblk * nchunks;
   long long cur = -1;
   // blocks outer when there are enough of them, else (block, chunk) items
-  const bool by_block = P.nblk >= 2LL * gridDim.x;
-  if (by_block) {
+  if (P.nblk >= 2LL * gridDim.x) {
     for (long long blk = blockIdx.x; blk < P.nblk; blk += gridDim.x) {
       eval_block<AR>(P, L, blk, nvec);
-      for (int c = 0; c < nchunks; ++c) apply_chunk<AR, NT, S>(P, L, x, y, nvec, nvdiv, blk, c);
+      for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, c);
       __syncthreads();
     }
   } else {
@@ -248,7 +330,7 @@ k_apply(const KPlan P, const typename Ar<AR>::T* __restrict__ x, typename Ar<AR>
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_chunk<AR, NT, S>(P, L, x, y, nvec, nvdiv, blk, (int)(w - blk * nchunks));
+      apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - blk * nchunks));
       __syncthreads();
     }
   }
@@ -268,12 +350,13 @@ struct BatchArgs {
   void* y[kBatchMax];
 };
 
-template <int AR, int NT, int S>
-__global__ void __launch_bounds__(NT)
-k_batch(const KPlan* __restrict__ plans, const BatchArgs A, long long nvec, NvDiv nvdiv, size_t lists_off) {
+template <int AR, int S, bool NV1>
+__global__ void __launch_bounds__(kNT, MinBlocks<AR>::v)
+k_batch(const KPlan* __restrict__ plans, const BatchArgs A, int nvec, NvDiv nvdiv, size_t lists_off) {
   extern __shared__ __align__(16) unsigned char sm[];
   KPlan& P = *reinterpret_cast<KPlan*>(sm);
-  using T = typename Ar<AR>::T;
+  using TX = typename Ar<AR>::TX;
+  using TY = typename Ar<AR>::TY;
   const long long total = A.blk_start[A.n];
   int inst = -1;
   Lists<AR> L{};
@@ -289,11 +372,14 @@ k_batch(const KPlan* __restrict__ plans, const BatchArgs A, long long nvec, NvDi
     }
     const long long blk = w - A.blk_start[inst];
     eval_block<AR>(P, L, blk, nvec);
-    const int nchunks = (int)((P.B * nvec + NT * S - 1) / (NT * S));
-    for (int c = 0; c < nchunks; ++c)
-      apply_chunk<AR, NT, S>(P, L, (const T*)A.x[inst], (T*)A.y[inst], nvec, nvdiv, blk, c);
+    const ChunkPlan cp = chunk_plan(P.B * nvec, S);
+    for (int c = 0; c < cp.count(); ++c)
+      apply_item<AR, S, NV1>(P, L, (const TX*)A.x[inst], (TY*)A.y[inst], nvec, nvdiv, blk, cp, c);
     __syncthreads();
   }
 }
+
+// FP64 input split into (hi, lo) float pairs, once per apply
+__global__ void k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n);
 
 }  // namespace hm

@@ -10,26 +10,24 @@
 namespace hm {
 
 struct Shape {
-  int nt, s, nchunks;
+  int s, nchunks;
 };
 
-// Threads per CTA and elements per thread for a block of `belems` elements:
-// the least padding (ragged last chunk), preferring more elements per thread
-// (memory-level parallelism) and at least 256 threads.
+// Elements per thread of the main chunks of a block of `belems` elements:
+// the most work in full S-chunks (more loads in flight per thread), the
+// remainder in single-element chunks (see chunk_plan).
 inline Shape pick_shape(long long belems) {
-  Shape best{256, 1, 1};
-  double bs = 1e30;
-  for (int nt : {512, 256, 128})
-    for (int s : {8, 4, 2, 1}) {
-      const long long chunk = (long long)nt * s;
-      const long long nch = (belems + chunk - 1) / chunk;
-      const double waste = (double)(nch * chunk) / (double)belems - 1.0;
-      const double score = waste + (s == 1 ? 0.05 : s == 2 ? 0.02 : 0.0) + (nt == 128 ? 0.02 : 0.0);
-      if (score < bs - 1e-12) {
-        bs = score;
-        best = {nt, s, (int)nch};
-      }
+  Shape best{2, chunk_plan((int)belems, 2).count()};
+  double bs = 0.0;
+  for (int s : {8, 6, 4, 3, 2}) {
+    const ChunkPlan cp = chunk_plan((int)belems, s);
+    const double frac = (double)cp.nS * kNT * s / (double)belems;   // share in S-chunks
+    const double score = frac * (1.0 + 0.02 * s);
+    if (score > bs + 1e-12) {
+      bs = score;
+      best = {s, cp.count()};
     }
+  }
   return best;
 }
 
@@ -50,43 +48,51 @@ inline NvDiv make_nvdiv(long long nvec) {
 
 int num_sms();
 
-template <int AR, int NT, int S>
-static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
-                                cudaStream_t st, int ctas) {
-  using T = typename Ar<AR>::T;
+template <int AR, int S, bool NV1>
+static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long nvec, int nchunks, cudaStream_t st,
+                             int ctas) {
+  using TX = typename Ar<AR>::TX;
+  using TY = typename Ar<AR>::TY;
   const size_t smem = lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag);
   static size_t attr_set = 0;
   if (smem > 48 * 1024 && smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<AR, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_apply<AR, S, NV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
   long long grid = ctas;
   if (grid <= 0) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<AR, NT, S>, NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<AR, S, NV1>, kNT, smem);
     grid = (long long)num_sms() * std::max(1, occ);
   }
   const long long items = k.nblk * nchunks;
   grid = std::max<long long>(1, std::min(grid, items));
-  k_apply<AR, NT, S><<<(unsigned)grid, NT, smem, st>>>(k, (const T*)x, (T*)y, nvec, make_nvdiv(nvec), nchunks);
+  k_apply<AR, S, NV1><<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec));
   return cudaGetLastError();
+}
+
+template <int AR, int S>
+static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
+                                cudaStream_t st, int ctas) {
+  if (nvec == 1) return launch_nv<AR, S, true>(k, x, y, nvec, nchunks, st, ctas);
+  return launch_nv<AR, S, false>(k, x, y, nvec, nchunks, st, ctas);
 }
 
 template <int AR>
 cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, int ctas) {
   const Shape sh = pick_shape((long long)k.B * nvec);
-#define HM_CASE(NT_, S_) \
-  if (sh.nt == NT_ && sh.s == S_) return launch_shape<AR, NT_, S_>(k, x, y, nvec, sh.nchunks, st, ctas);
-  HM_CASE(512, 8) HM_CASE(512, 4) HM_CASE(512, 2) HM_CASE(512, 1)
-  HM_CASE(256, 8) HM_CASE(256, 4) HM_CASE(256, 2) HM_CASE(256, 1)
-  HM_CASE(128, 8) HM_CASE(128, 4) HM_CASE(128, 2) HM_CASE(128, 1)
-#undef HM_CASE
-  return cudaErrorInvalidConfiguration;
+  switch (sh.s) {
+    case 8: return launch_shape<AR, 8>(k, x, y, nvec, sh.nchunks, st, ctas);
+    case 6: return launch_shape<AR, 6>(k, x, y, nvec, sh.nchunks, st, ctas);
+    case 4: return launch_shape<AR, 4>(k, x, y, nvec, sh.nchunks, st, ctas);
+    case 3: return launch_shape<AR, 3>(k, x, y, nvec, sh.nchunks, st, ctas);
+    default: return launch_shape<AR, 2>(k, x, y, nvec, sh.nchunks, st, ctas);
+  }
 }
 
-template <int AR, int NT, int S>
-static cudaError_t batch_shape(const KPlan* dplans, const std::vector<const Plan*>& members,
+template <int AR, int S, bool NV1>
+static cudaError_t batch_nv(const KPlan* dplans, const std::vector<const Plan*>& members,
                                const void* const* xs, void* const* ys, long long nvec, cudaStream_t st) {
   size_t lists = 0;
   for (const Plan* p : members) {
@@ -97,12 +103,12 @@ static cudaError_t batch_shape(const KPlan* dplans, const std::vector<const Plan
   const size_t smem = off + lists;
   static size_t attr_set = 0;
   if (smem > 48 * 1024 && smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch<AR, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batch<AR, S, NV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<AR, NT, S>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<AR, S, NV1>, kNT, smem);
   const int n = (int)members.size();
   for (int c0 = 0; c0 < n; c0 += kBatchMax) {
     BatchArgs A{};
@@ -115,14 +121,21 @@ static cudaError_t batch_shape(const KPlan* dplans, const std::vector<const Plan
     }
     long long grid = (long long)num_sms() * std::max(1, occ);
     grid = std::max<long long>(1, std::min(grid, A.blk_start[A.n]));
-    k_batch<AR, NT, S><<<(unsigned)grid, NT, smem, st>>>(dplans + c0, A, nvec, make_nvdiv(nvec), off);
+    k_batch<AR, S, NV1><<<(unsigned)grid, kNT, smem, st>>>(dplans + c0, A, (int)nvec, make_nvdiv(nvec), off);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// One (NT, S) for the whole batch, chosen on the median block size.
+template <int AR, int S>
+static cudaError_t batch_shape(const KPlan* dplans, const std::vector<const Plan*>& members,
+                               const void* const* xs, void* const* ys, long long nvec, cudaStream_t st) {
+  if (nvec == 1) return batch_nv<AR, S, true>(dplans, members, xs, ys, nvec, st);
+  return batch_nv<AR, S, false>(dplans, members, xs, ys, nvec, st);
+}
+
+// One elements-per-thread count for the whole batch, chosen on the median block size.
 template <int AR>
 cudaError_t launch_batch_t(const KPlan* dplans, const std::vector<const Plan*>& members, const void* const* xs,
                            void* const* ys, long long nvec, cudaStream_t st) {
@@ -130,13 +143,13 @@ cudaError_t launch_batch_t(const KPlan* dplans, const std::vector<const Plan*>& 
   for (const Plan* p : members) be.push_back((long long)p->B * nvec);
   std::nth_element(be.begin(), be.begin() + be.size() / 2, be.end());
   const Shape sh = pick_shape(be[be.size() / 2]);
-#define HM_CASE(NT_, S_) \
-  if (sh.nt == NT_ && sh.s == S_) return batch_shape<AR, NT_, S_>(dplans, members, xs, ys, nvec, st);
-  HM_CASE(512, 8) HM_CASE(512, 4) HM_CASE(512, 2) HM_CASE(512, 1)
-  HM_CASE(256, 8) HM_CASE(256, 4) HM_CASE(256, 2) HM_CASE(256, 1)
-  HM_CASE(128, 8) HM_CASE(128, 4) HM_CASE(128, 2) HM_CASE(128, 1)
-#undef HM_CASE
-  return cudaErrorInvalidConfiguration;
+  switch (sh.s) {
+    case 8: return batch_shape<AR, 8>(dplans, members, xs, ys, nvec, st);
+    case 6: return batch_shape<AR, 6>(dplans, members, xs, ys, nvec, st);
+    case 4: return batch_shape<AR, 4>(dplans, members, xs, ys, nvec, st);
+    case 3: return batch_shape<AR, 3>(dplans, members, xs, ys, nvec, st);
+    default: return batch_shape<AR, 2>(dplans, members, xs, ys, nvec, st);
+  }
 }
 
 }  // namespace hm

@@ -26,8 +26,6 @@ static Plan* as_plan(hm_handle h) {
   return p;
 }
 
-cudaError_t apply_kplan(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt,
-                        cudaStream_t s, int ctas, bool native_f64);
 
 static size_t esize(hm_dtype dt) { return dt == HM_F32 ? 4 : 8; }
 
@@ -145,9 +143,7 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
   const KPlan& k = (flags & 2) ? p->kt : p->k;
-  cudaError_t e = apply_kplan(k, x, y, nvec, dtype, (cudaStream_t)stream, ctas, (flags & 1) != 0);
-  if (e != cudaSuccess) return cuda_fail(e, "apply launch");
-  return HM_OK;
+  return apply_on(p, k, x, y, nvec, dtype, (cudaStream_t)stream, ctas, (flags & 1) != 0);
 }
 
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
@@ -235,6 +231,7 @@ int hm_destroy(hm_handle h) {
   cudaDeviceSynchronize();
   free_plan_device(p);
   if (p->scratch) cudaFree(p->scratch);
+  if (p->xsplit) cudaFree(p->xsplit);
   if (p->batch_dev) cudaFree(p->batch_dev);
   p->magic = 0;
   delete p;

@@ -2,12 +2,14 @@
 //
 // Arithmetic policies:
 //   AR_F32  : FP32 storage, FP32 accumulation.
-//   AR_DF64 : FP64 storage, accumulation in an unevaluated sum of two floats
-//             ("double-float", Dekker 1971; TwoSum of Knuth TAOCP vol. 2,
-//             4.2.2). GB300 executes FP64 FMA at ~1/70 of the FP32 rate and
-//             its f64<->f32 conversions run on the same slow pipe, so doubles
-//             are split into float pairs and rebuilt with integer bit
-//             operations only. Relative accuracy ~2^-46 per product.
+//   AR_DF64 : FP64 storage. GB300 executes FP64 FMA at ~1/70 of the FP32 rate
+//             and its f64<->f32 conversions run on the same slow pipe, so each
+//             double is split once per apply into a pair of floats (integer
+//             bit operations only; a separate pass) and the kernel accumulates
+//             an unevaluated sum of two floats ("double-float": Dekker 1971;
+//             TwoSum of Knuth, TAOCP vol. 2, 4.2.2). Relative accuracy about
+//             2^-46 per product; the result is rebuilt as a double with one
+//             FP64 add.
 //   AR_F64  : FP64 storage, native FP64 accumulation (reference variant).
 #pragma once
 
@@ -25,34 +27,49 @@ struct DF {  // unevaluated sum s + c
 };
 
 // Split a double into hi (truncated to 24 significant bits) and lo (the next
-// 23 bits, truncated) using integer operations only. Exact range handling:
+// 23 bits, truncated): x = hi + lo + r with |r| < 2^-46 |x|. Integer
+// operations only. Fast path for 2^-80 <= |x| < 2^128; the rare remainder
+// (zero, tiny, huge, inf, nan) takes a slower exact-range branch:
 // |x| < 2^-126 -> (0, 0); |x| < 2^-80 -> lo = 0; |x| >= 2^128 -> inf/nan.
-__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+__device__ __forceinline__ float2 split_f64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
-  const unsigned E = (h >> 20) & 0x7FFu;
   const unsigned sign = h & 0x80000000u;
-  const unsigned mant = ((h & 0xFFFFFu) << 3) | (l >> 29);
-  const unsigned hb = sign | ((E - 896u) << 23) | mant;
+  // funnel shift: bits 31..23 hold the low 9 bits of the double exponent E;
+  // E - 896 is the float exponent, and E mod 512 = (E - 896 + 384) mod 512
+  const unsigned t = __funnelshift_l(l, h, 3) - 0xC0000000u;
+  const unsigned hb = (t & 0x7FFFFFFFu) | sign;
   const float ft = __fsub_rn(__uint_as_float(0x4B000000u | ((l >> 6) & 0x7FFFFFu)), 8388608.0f);
-  const float scale = __uint_as_float(sign | ((E - 942u) << 23));
-  const bool hnorm = (E >= 897u) & (E <= 1150u);
-  const bool lnorm = (E >= 943u) & (E <= 1150u);
-  const unsigned special = (E > 1150u) ? (sign | 0x7F800000u | ((E == 2047u && ((h & 0xFFFFFu) | l)) ? 0x400000u : 0u))
-                                       : sign;
-  hi = __uint_as_float(hnorm ? hb : special);
-  lo = lnorm ? __fmul_rn(ft, scale) : 0.0f;
+  const unsigned scale = (hb & 0xFF800000u) - (46u << 23);
+  float hi = __uint_as_float(hb);
+  float lo = __fmul_rn(ft, __uint_as_float(scale));
+  const unsigned ax = h & 0x7FFFFFFFu;
+  if (ax - (943u << 20) >= ((1151u - 943u) << 20)) {  // outside [2^-80, 2^128)
+    const unsigned E = ax >> 20;
+    if (E >= 897u && E <= 1150u) {
+      lo = 0.0f;                          // hi is exact, lo would be subnormal
+    } else if (E < 897u) {
+      hi = __uint_as_float(sign);
+      lo = 0.0f;
+    } else {
+      hi = __uint_as_float(sign | 0x7F800000u | ((E == 2047u && ((h & 0xFFFFFu) | l)) ? 0x400000u : 0u));
+      lo = 0.0f;
+    }
+  }
+  return make_float2(hi, lo);
 }
 
 // Exact float -> double by bit manipulation (denormal floats flush to 0).
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  const unsigned sign = u & 0x80000000u;
-  unsigned hi = sign | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  const unsigned a = u & 0x7FFFFFFFu;
+  unsigned hi = (u & 0x80000000u) | ((a >> 3) + (896u << 20));
   unsigned lo = u << 29;
-  if (e == 0u) { hi = sign; lo = 0u; }
-  if (e == 255u) { hi = sign | 0x7FF00000u | ((u & 0x7FFFFFu) ? 0x80000u : 0u); lo = 0u; }
+  if (a - 0x00800000u >= 0x7F000000u) {  // zero, subnormal, inf or nan
+    const unsigned e = a >> 23;
+    hi = (u & 0x80000000u) | (e == 255u ? (0x7FF00000u | ((a & 0x7FFFFFu) ? 0x80000u : 0u)) : 0u);
+    lo = 0u;
+  }
   return __hiloint2double((int)hi, (int)lo);
 }
 
@@ -93,80 +110,75 @@ __device__ __forceinline__ double df_to_double(DF a) {
 }
 
 // ---------------------------------------------------------------------------
-// Arithmetic policies
+// Arithmetic policies. TX: input storage as the kernel reads it; TY: output
+// storage; C: coefficient; E: packed ELL entry {delta, coefficient}.
 // ---------------------------------------------------------------------------
 template <int AR> struct Ar;
 
 template <> struct Ar<AR_F32> {
-  using T = float;     // storage
-  using C = float;     // coefficient
-  using Acc = float;   // accumulator
-  using X = float;     // prepared input value
-  using Dsum = float;  // diagonal sum
+  using TX = float;
+  using TY = float;
+  using C = float;
+  using Acc = float;
+  using Dsum = float;
+  using E = int2;
   __device__ static const C* tab(const KPlan& P) { return P.tab_f; }
   __device__ static const C* diag(const KPlan& P) { return P.diag_f; }
-  __device__ static const C* ell(const KPlan& P) { return P.ell_f; }
-  __device__ static const C* ttab(const KPlan& P) { return P.ttab_f; }
-  __device__ static C czero() { return 0.0f; }
+  __device__ static const E* ell(const KPlan& P) { return (const E*)P.ell_pf; }
+  __device__ static int ell_delta(E e) { return e.x; }
+  __device__ static C ell_coef(E e) { return __int_as_float(e.y); }
   __device__ static bool nz(C c) { return c != 0.0f; }
-  __device__ static X prep(T v) { return v; }
   __device__ static Acc azero() { return 0.0f; }
-  __device__ static void fma(Acc& a, C c, X x) { a = __fmaf_rn(c, x, a); }
+  __device__ static void fma(Acc& a, C c, TX x) { a = __fmaf_rn(c, x, a); }
   __device__ static Dsum dzero() { return 0.0f; }
   __device__ static void dadd(Dsum& d, C c) { d = __fadd_rn(d, c); }
-  __device__ static Acc dmul(Dsum d, X x) { return __fmul_rn(d, x); }
+  __device__ static Acc dmul(Dsum d, TX x) { return __fmul_rn(d, x); }
   __device__ static void dmadd(Dsum& d, C v, Dsum u) { d = __fmaf_rn(v, u, d); }
   __device__ static void acc_mul(Acc& a, C v, Acc g) { a = __fmaf_rn(v, g, a); }
-  __device__ static T out(Acc a) { return a; }
-  __device__ static double to_double(X x) { return (double)x; }
+  __device__ static TY out(Acc a) { return a; }
 };
 
 template <> struct Ar<AR_F64> {
-  using T = double;
+  using TX = double;
+  using TY = double;
   using C = double;
   using Acc = double;
-  using X = double;
   using Dsum = double;
+  using E = int4;
   __device__ static const C* tab(const KPlan& P) { return P.tab_d; }
   __device__ static const C* diag(const KPlan& P) { return P.diag_d; }
-  __device__ static const C* ell(const KPlan& P) { return P.ell_d; }
-  __device__ static const C* ttab(const KPlan& P) { return P.ttab_d; }
-  __device__ static C czero() { return 0.0; }
+  __device__ static const E* ell(const KPlan& P) { return (const E*)P.ell_pd; }
+  __device__ static int ell_delta(E e) { return e.x; }
+  __device__ static C ell_coef(E e) { return __hiloint2double(e.w, e.z); }
   __device__ static bool nz(C c) { return c != 0.0; }
-  __device__ static X prep(T v) { return v; }
   __device__ static Acc azero() { return 0.0; }
-  __device__ static void fma(Acc& a, C c, X x) { a = __fma_rn(c, x, a); }
+  __device__ static void fma(Acc& a, C c, TX x) { a = __fma_rn(c, x, a); }
   __device__ static Dsum dzero() { return 0.0; }
   __device__ static void dadd(Dsum& d, C c) { d = __dadd_rn(d, c); }
-  __device__ static Acc dmul(Dsum d, X x) { return __dmul_rn(d, x); }
+  __device__ static Acc dmul(Dsum d, TX x) { return __dmul_rn(d, x); }
   __device__ static void dmadd(Dsum& d, C v, Dsum u) { d = __fma_rn(v, u, d); }
   __device__ static void acc_mul(Acc& a, C v, Acc g) { a = __fma_rn(v, g, a); }
-  __device__ static T out(Acc a) { return a; }
-  __device__ static double to_double(X x) { return x; }
+  __device__ static TY out(Acc a) { return a; }
 };
 
 template <> struct Ar<AR_DF64> {
-  using T = double;
+  using TX = float2;  // pre-split (hi, lo) input
+  using TY = double;
   using C = float2;
   using Acc = DF;
-  using X = float2;
   using Dsum = DF;
+  using E = int4;
   __device__ static const C* tab(const KPlan& P) { return P.tab_df; }
   __device__ static const C* diag(const KPlan& P) { return P.diag_df; }
-  __device__ static const C* ell(const KPlan& P) { return P.ell_df; }
-  __device__ static const C* ttab(const KPlan& P) { return P.ttab_df; }
-  __device__ static C czero() { return make_float2(0.f, 0.f); }
+  __device__ static const E* ell(const KPlan& P) { return (const E*)P.ell_pdf; }
+  __device__ static int ell_delta(E e) { return e.x; }
+  __device__ static C ell_coef(E e) { return make_float2(__int_as_float(e.z), __int_as_float(e.w)); }
   __device__ static bool nz(C c) { return c.x != 0.0f; }
-  __device__ static X prep(T v) {
-    float h, l;
-    split_f64(v, h, l);
-    return make_float2(h, l);
-  }
   __device__ static Acc azero() { return DF{0.f, 0.f}; }
-  __device__ static void fma(Acc& a, C c, X x) { df_fma(a, c, x.x, x.y); }
+  __device__ static void fma(Acc& a, C c, TX x) { df_fma(a, c, x.x, x.y); }
   __device__ static Dsum dzero() { return DF{0.f, 0.f}; }
   __device__ static void dadd(Dsum& d, C c) { df_add(d, c); }
-  __device__ static Acc dmul(Dsum d, X x) {
+  __device__ static Acc dmul(Dsum d, TX x) {
     DF a{0.f, 0.f};
     df_fma(a, df_norm(d), x.x, x.y);
     return a;
@@ -179,51 +191,8 @@ template <> struct Ar<AR_DF64> {
     const float2 n = df_norm(g);
     df_fma(a, v, n.x, n.y);
   }
-  __device__ static T out(Acc a) { return df_to_double(a); }
-  __device__ static double to_double(X x) { return f2d_exact(x.x) + f2d_exact(x.y); }
+  __device__ static TY out(Acc a) { return df_to_double(a); }
 };
-
-// ---------------------------------------------------------------------------
-// Vector loads/stores of NV consecutive values (alignment checked on the host)
-// ---------------------------------------------------------------------------
-template <class T, int NV>
-__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&v)[NV]) {
-  constexpr int bytes = NV * (int)sizeof(T);
-  if constexpr (bytes % 16 == 0) {
-#pragma unroll
-    for (int u = 0; u < NV; u += 16 / (int)sizeof(T)) {
-      const uint4 q = __ldg(reinterpret_cast<const uint4*>(p + u));
-      const T* t = reinterpret_cast<const T*>(&q);
-#pragma unroll
-      for (int w = 0; w < 16 / (int)sizeof(T); ++w) v[u + w] = t[w];
-    }
-  } else if constexpr (bytes == 8 && sizeof(T) == 4) {
-    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
-    v[0] = q.x;
-    v[1] = q.y;
-  } else {
-#pragma unroll
-    for (int u = 0; u < NV; ++u) v[u] = __ldg(p + u);
-  }
-}
-
-template <class T, int NV>
-__device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[NV]) {
-  constexpr int bytes = NV * (int)sizeof(T);
-  if constexpr (bytes % 16 == 0) {
-#pragma unroll
-    for (int u = 0; u < NV; u += 16 / (int)sizeof(T)) {
-      uint4 q;
-      T* t = reinterpret_cast<T*>(&q);
-#pragma unroll
-      for (int w = 0; w < 16 / (int)sizeof(T); ++w) t[w] = v[u + w];
-      *reinterpret_cast<uint4*>(p + u) = q;
-    }
-  } else {
-#pragma unroll
-    for (int u = 0; u < NV; ++u) p[u] = v[u];
-  }
-}
 
 // digit of a high (tile-uniform) site, held by lane (site % 32) in nh0/nh1
 __device__ __forceinline__ int high_digit(int site, int nh0, int nh1) {

@@ -97,16 +97,15 @@ struct KPlan {
   const KGroup* grp;
   const KMember* mem;
   const uint32_t* ptab;   // [B] packed low digits of each low index
-  const int* ell_delta;   // [ell_w * B], w-major
+  const int2* ell_pf;     // [ell_w * B] packed {delta, coef} (w-major), FP32
+  const int4* ell_pdf;    // {delta, 0, coef.hi, coef.lo}, double-float
+  const int4* ell_pd;     // {delta, 0, double coef}, native FP64
   const double* tab_d;    // coefficient pool (HH tables, u and v tables)
   const float2* tab_df;
   const float* tab_f;
   const double* diag_d;   // [B] diagonal from low-only channels (+ constants)
   const float2* diag_df;
   const float* diag_f;
-  const double* ell_d;    // [ell_w * B]
-  const float2* ell_df;
-  const float* ell_f;
   const KTermChan* tch;   // [nterm_ch]
   const double* ttab_d;   // per-term tables
   const float2* ttab_df;
@@ -141,6 +140,10 @@ struct Plan {
   void* dev = nullptr;        // one device allocation holding every table
   size_t dev_bytes = 0;
 
+  // FP64 input split into float pairs, one vector (grown on demand)
+  void* xsplit = nullptr;
+  size_t xsplit_bytes = 0;
+
   // scratch for the adjoint reduction (grown on demand)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -166,8 +169,10 @@ void set_error(const std::string& s);
 int cuda_fail(cudaError_t e, const char* what);
 
 // kernels (apply.cu / adjoint.cu / lanczos.cu / batch.cu)
-int launch_apply(const Plan* p, const void* x, void* y, long long nvec, hm_dtype dt,
-                 cudaStream_t s, int ctas_override);
+int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+                 int ctas_override);
+int apply_on(Plan* p, const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+             int ctas, bool native_f64);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
 int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,

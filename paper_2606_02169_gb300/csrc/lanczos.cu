@@ -18,8 +18,6 @@
 
 namespace hm {
 
-cudaError_t apply_kplan(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt,
-                        cudaStream_t s, int ctas, bool native_f64);
 
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
@@ -232,8 +230,8 @@ static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, do
     for (int k = 0; k < m; ++k) {
       if (psi) k_axpy<T><<<vb, 256, 0, s>>>(psi, vk, (*u)[k], n);
       auto it = p->tuned.find({(int)dt, 1LL});
-      cudaError_t le = apply_kplan(p->k, vk, w, 1, dt, s, it == p->tuned.end() ? 0 : it->second, false);
-      if (le != cudaSuccess) return cuda_fail(le, "Lanczos apply");
+      int arc = apply_on(p, p->k, vk, w, 1, dt, s, it == p->tuned.end() ? 0 : it->second, false);
+      if (arc) return arc;
       dot(vk, w, dal + k, 0);
       k_axpy2<T><<<vb, 256, 0, s>>>(w, vk, k > 0 ? vp : nullptr, dal + k, k > 0 ? dbe + k - 1 : nullptr, n);
       if (flags & 1) {  // local reorthogonalisation (second Gram-Schmidt pass)

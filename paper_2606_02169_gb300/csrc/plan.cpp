@@ -637,14 +637,31 @@ int build_plan(Plan* p) {
     cur += std::max<size_t>(bytes, 1);
     return o;
   };
-  std::vector<float2> tabdf[2], diagdf[2], elldf[2];
-  std::vector<float> tabf[2], diagf[2], ellf[2];
+  std::vector<float2> tabdf[2], diagdf[2];
+  std::vector<float> tabf[2], diagf[2];
   const HostTables* HT[2] = {&Hf, p->hermitian ? &Hf : &Ht};
   for (int s = 0; s < 2; ++s) {
     const HostTables& H = *HT[s];
     for (double v : H.tab) { tabdf[s].push_back(split_df(v)); tabf[s].push_back((float)v); }
     for (double v : H.diag) { diagdf[s].push_back(split_df(v)); diagf[s].push_back((float)v); }
-    for (double v : H.ell) { elldf[s].push_back(split_df(v)); ellf[s].push_back((float)v); }
+  }
+  // packed ELL entries {delta, coefficient}; padding is {0, 0} (own element, zero weight)
+  std::vector<int32_t> ellpf[2], ellpdf[2], ellpd[2];
+  for (int s = 0; s < 2; ++s) {
+    const HostTables& H = *HT[s];
+    for (size_t e = 0; e < H.ell.size(); ++e) {
+      const double v = H.ell[e];
+      const float f = (float)v;
+      const float2 df = split_df(v);
+      int32_t fb, hb, lb, w[2];
+      std::memcpy(&fb, &f, 4);
+      std::memcpy(&hb, &df.x, 4);
+      std::memcpy(&lb, &df.y, 4);
+      std::memcpy(w, &v, 8);
+      ellpf[s].insert(ellpf[s].end(), {H.ell_delta[e], fb});
+      ellpdf[s].insert(ellpdf[s].end(), {H.ell_delta[e], 0, hb, lb});
+      ellpd[s].insert(ellpd[s].end(), {H.ell_delta[e], 0, w[0], w[1]});
+    }
   }
   std::vector<float2> ttabdf;
   std::vector<float> ttabf;
@@ -661,16 +678,15 @@ int build_plan(Plan* p) {
   for (int s = 0; s < nsets; ++s) {
     const HostTables& H = *HT[s];
     o[s][0] = add(H.kch.data(), H.kch.size() * sizeof(KChan));
-    o[s][1] = add(H.ell_delta.data(), H.ell_delta.size() * 4);
+    o[s][1] = add(ellpf[s].data(), ellpf[s].size() * 4);
     o[s][2] = add(H.tab.data(), H.tab.size() * 8);
     o[s][3] = add(tabdf[s].data(), tabdf[s].size() * 8);
     o[s][4] = add(tabf[s].data(), tabf[s].size() * 4);
     o[s][5] = add(H.diag.data(), H.diag.size() * 8);
     o[s][6] = add(diagdf[s].data(), diagdf[s].size() * 8);
     o[s][7] = add(diagf[s].data(), diagf[s].size() * 4);
-    o[s][8] = add(H.ell.data(), H.ell.size() * 8);
-    o[s][9] = add(elldf[s].data(), elldf[s].size() * 8);
-    o[s][10] = add(ellf[s].data(), ellf[s].size() * 4);
+    o[s][8] = add(ellpdf[s].data(), ellpdf[s].size() * 4);
+    o[s][9] = add(ellpd[s].data(), ellpd[s].size() * 4);
     o[s][11] = add(H.grp.data(), H.grp.size() * sizeof(KGroup));
     o[s][12] = add(H.mem.data(), H.mem.size() * sizeof(KMember));
   }
@@ -712,16 +728,15 @@ int build_plan(Plan* p) {
     k.sites = (const KSite*)P(o_sites);
     k.ch = (const KChan*)P(o[ss][0]);
     k.ptab = (const uint32_t*)P(o_ptab);
-    k.ell_delta = (const int*)P(o[ss][1]);
+    k.ell_pf = (const int2*)P(o[ss][1]);
     k.tab_d = (const double*)P(o[ss][2]);
     k.tab_df = (const float2*)P(o[ss][3]);
     k.tab_f = (const float*)P(o[ss][4]);
     k.diag_d = (const double*)P(o[ss][5]);
     k.diag_df = (const float2*)P(o[ss][6]);
     k.diag_f = (const float*)P(o[ss][7]);
-    k.ell_d = (const double*)P(o[ss][8]);
-    k.ell_df = (const float2*)P(o[ss][9]);
-    k.ell_f = (const float*)P(o[ss][10]);
+    k.ell_pdf = (const int4*)P(o[ss][8]);
+    k.ell_pd = (const int4*)P(o[ss][9]);
     k.grp = (const KGroup*)P(o[ss][11]);
     k.mem = (const KMember*)P(o[ss][12]);
     k.tch = (const KTermChan*)P(o_tch);
