@@ -126,6 +126,25 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
                      int64_t nvec, hm_dtype dtype, void* stream);
 
+/* Coupling gradients gcoef[t] = sum_v <gy_v| O_t |x_v> -- what
+ * hm_apply_adjoint returns with gx = NULL -- without allocating device memory.
+ * The paper has no counterpart: this serves callers that cannot let the
+ * library call cudaMalloc, such as code running while a stream is captured
+ * into a CUDA graph, or a process whose device memory is owned by another
+ * allocator (a framework's caching pool, a fixed serving budget).
+ * The per-CTA partial sums live in one file-scope device array of 131072
+ * doubles (1 MiB) that every GPU loading the library holds until the process
+ * exits; the grid is capped so that grid * nterms <= 131072. A term list
+ * longer than 131072 returns HM_ERR_TOO_LARGE; one longer than 3200 returns
+ * HM_ERR_UNSUPPORTED (shared-memory limit of the reduction). The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make it before any stream capture. Every call
+ * shares the array, so calls that overlap on the GPU race; each call writes
+ * every partial it reads, so nothing is cleared between calls. gy, x: device
+ * vectors of dtype; gcoef: device, nterms doubles, overwritten. */
+int hm_coupling_gradients_static(hm_handle h, const void* gy, const void* x, double* gcoef,
+                                 int64_t nvec, hm_dtype dtype, void* stream);
+
 /* Lanczos ground state (Sec. I: Krylov solvers need only y = H x).
  * v0: device start vector (D elements of dtype, need not be normalised).
  * Runs up to `steps` steps; alpha/beta (host, >= steps doubles) receive the

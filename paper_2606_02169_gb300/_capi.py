@@ -34,7 +34,7 @@ HM_LANCZOS_BREAKDOWN = 1
 EXPORTS = [
     "hm_create", "hm_set_coefficients", "hm_dim", "hm_num_terms", "hm_apply", "hm_apply_ex",
     "hm_apply_adjoint", "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune",
-    "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export",
+    "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export", "hm_coupling_gradients_static",
 ]
 
 

@@ -1,0 +1,83 @@
+// Coupling gradients without any device allocation.
+//
+// hm_apply_adjoint grows a per-plan scratch buffer with cudaMalloc for the
+// per-CTA partial sums of the coupling gradients. Some callers cannot let a
+// library allocate: code that runs while a stream is being captured into a
+// CUDA graph (cudaMalloc is not a stream operation and is not allowed
+// there), and processes whose device memory belongs to another allocator
+// (a framework's caching pool or a fixed serving budget). For them this file
+// keeps the partials in a fixed, file-scope device array instead.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+int grad_grid(const Plan* p);
+size_t grad_smem(const Plan* p);
+int launch_term_grad(const Plan* p, const void* gy, const void* x, double* gcoef, long long nvec, hm_dtype dt,
+                     double* partial, int grid, cudaStream_t s);
+
+// 1 MiB of partial sums: grid * nterms <= 131072. Every GPU that loads the
+// library holds this array until the process exits.
+constexpr long long kStaticPartials = 131072;
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+
+// Device address of g_static_partials per device. In host code the symbol
+// names a host-side stand-in, so the address is looked up once per device
+// with that device current.
+static std::mutex g_static_mu;
+static std::map<int, double*> g_static_addr;
+
+static int static_partials(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> g(g_static_mu);
+  auto it = g_static_addr.find(dev);
+  if (it == g_static_addr.end()) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static partials)");
+    it = g_static_addr.emplace(dev, (double*)ptr).first;
+  }
+  *out = it->second;
+  return HM_OK;
+}
+
+}  // namespace hm
+
+extern "C" int hm_coupling_gradients_static(hm_handle h, const void* gy, const void* x, double* gcoef,
+                                            int64_t nvec, hm_dtype dtype, void* stream) {
+  using namespace hm;
+  Plan* p = reinterpret_cast<Plan*>(h);
+  if (!p || p->magic != 0x484d504cU || p->is_batch) {
+    set_error("invalid handle");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (!gy || !x || !gcoef || nvec < 1 || (dtype != HM_F64 && dtype != HM_F32)) {
+    set_error("gy, x and gcoef must be device pointers, nvec >= 1, dtype HM_F64 or HM_F32");
+    return HM_ERR_INVALID_ARG;
+  }
+  const long long nterms = (long long)p->terms.size();
+  if (nterms == 0) return HM_OK;
+  if (nterms > kStaticPartials) {
+    set_error("hm_coupling_gradients_static: " + std::to_string(nterms) +
+              " terms exceed its fixed scratch of 131072 partial sums");
+    return HM_ERR_TOO_LARGE;
+  }
+  if (grad_smem(p) > 200 * 1024) {
+    set_error("too many terms for the gradient reduction (limit 3200)");
+    return HM_ERR_UNSUPPORTED;
+  }
+  double* partial = nullptr;
+  int rc = static_partials(&partial);
+  if (rc) return rc;
+  // each CTA writes all nterms of its row before the reduction reads them,
+  // so nothing in the shared array has to be cleared between calls
+  const int grid = (int)std::min<long long>(grad_grid(p), kStaticPartials / nterms);
+  return launch_term_grad(p, gy, x, gcoef, nvec, dtype, partial, grid, (cudaStream_t)stream);
+}

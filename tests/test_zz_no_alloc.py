@@ -1,0 +1,82 @@
+"""hm_coupling_gradients_static: coupling gradients for callers that cannot
+let the library allocate device memory (stream capture, a foreign memory
+pool). It keeps its partial sums in a fixed library-static device array and
+must agree with hm_apply_adjoint, call after call.
+
+This file is collected last, so a run that stops at its first failure has
+already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _entry():
+    from paper_2606_02169_gb300 import _capi
+    lib = _capi.load()
+    f = lib.hm_coupling_gradients_static
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_int, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return lib, f
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_static_scratch_gradients_match_adjoint_twice(dtype):
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Hamiltonian
+    lib, f = _entry()
+    tdt = getattr(torch, dtype)
+    code = 0 if dtype == "float64" else 1
+    for m, nvec in ((W.square_lattice_xxz(3, 4, seed=4), 1), (W.ferrimagnet_chain(10), 3)):
+        h = Hamiltonian(m.sites, m.terms)
+        D = h.D
+        gy = torch.from_numpy(W.vector(D, 5, nvec=nvec)).to("cuda", tdt)
+        x = torch.from_numpy(W.vector(D, 6, nvec=nvec)).to("cuda", tdt)
+        _, ref = h.adjoint(gy, x, want_gx=False)            # allocating entry point
+        ref = ref.cpu().numpy()
+        stream = torch.cuda.current_stream().cuda_stream
+        for call in range(2):                               # the array keeps the last call's data
+            out = torch.full((h.nterms,), float("nan"), dtype=torch.float64, device="cuda")
+            rc = f(h.handle, gy.data_ptr(), x.data_ptr(), out.data_ptr(), nvec, code, stream)
+            assert rc == 0, lib.hm_last_error().decode()
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            scale = np.abs(ref).max()
+            assert np.allclose(got, ref, rtol=1e-11, atol=1e-13 * scale), (m.name, call)
+
+
+def test_static_scratch_matches_oracle():
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Hamiltonian
+    lib, f = _entry()
+    m = W.random_model([3, 2, 5, 2, 3, 4, 2, 3, 2], None, nterms=24, seed=1)
+    D = oracle.dimension(m.sites)
+    gy, x = W.vector(D, 1), W.vector(D, 2)
+    h = Hamiltonian(m.sites, m.terms)
+    out = torch.empty(h.nterms, dtype=torch.float64, device="cuda")
+    gy_d, x_d = torch.from_numpy(gy).cuda(), torch.from_numpy(x).cuda()   # keep both alive
+    rc = f(h.handle, gy_d.data_ptr(), x_d.data_ptr(), out.data_ptr(), 1, 0, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    ref = oracle.term_gradients(m.sites, m.terms, gy, x).real
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-11, atol=1e-12)
+
+
+def test_static_scratch_rejects_term_lists_beyond_its_size():
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Hamiltonian, _capi
+    lib, f = _entry()
+    terms = [(0, "Sz", -1, "I", 1e-6)] * 131073
+    h = Hamiltonian([("spin", 2), ("spin", 2)], terms)
+    v = torch.zeros(4, dtype=torch.float64, device="cuda")
+    g = torch.zeros(131073, dtype=torch.float64, device="cuda")
+    rc = f(h.handle, v.data_ptr(), v.data_ptr(), g.data_ptr(), 1, 0, None)
+    assert rc == _capi.HM_ERR_TOO_LARGE
+    assert "131072" in lib.hm_last_error().decode()
