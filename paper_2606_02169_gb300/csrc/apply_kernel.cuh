@@ -37,6 +37,10 @@ struct Lists {  // per-block uniform values (shared memory)
   C* mem_u;             // [n_mem] high factor u of each group member
   long long* mem_src;   // [n_mem] element offset of each member's source
   int* mem_ok;          // [n_mem] source range of this block inside the vector
+  C* gact_u;            // [n_mem] active members of each group, compacted in place
+  long long* gact_src;  //        within the group's member range [m0, m0 + gact_n)
+  int* gact_n;          // [n_grp_diag + n_grp] number of active members
+  int* gact_ok;         // [n_grp_diag + n_grp] every active source range inside the vector
   int* grp_v;           // [n_grp_diag + n_grp] v row base
   Dsum* grp_U;          // [n_grp_diag] sum of member u (diagonal groups)
   Dsum* du;             // [1] sum of high diagonal channels
@@ -47,8 +51,8 @@ __host__ __device__ inline size_t lists_bytes(int n_hh, int n_mem, int n_grp, in
   using C = typename Ar<AR>::C;
   using Dsum = typename Ar<AR>::Dsum;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return al(64 * 4) + 2 * al(n_hh * sizeof(C)) + 2 * al(n_hh * 8) + al(16) + al(n_mem * sizeof(C)) + al(n_mem * 8) +
-         al(n_mem * 4) + al(n_grp * 4) + al(n_grpd * sizeof(Dsum)) + al(sizeof(Dsum));
+  return al(64 * 4) + 2 * al(n_hh * sizeof(C)) + 2 * al(n_hh * 8) + al(16) + 2 * al(n_mem * sizeof(C)) +
+         2 * al(n_mem * 8) + al(n_mem * 4) + 3 * al(n_grp * 4) + al(n_grpd * sizeof(Dsum)) + al(sizeof(Dsum));
 }
 
 template <int AR>
@@ -76,6 +80,14 @@ __device__ inline Lists<AR> carve(unsigned char* sm, int n_hh, int n_mem, int n_
   o += al(n_mem * 8);
   L.mem_ok = (int*)(sm + o);
   o += al(n_mem * 4);
+  L.gact_u = (C*)(sm + o);
+  o += al(n_mem * sizeof(C));
+  L.gact_src = (long long*)(sm + o);
+  o += al(n_mem * 8);
+  L.gact_n = (int*)(sm + o);
+  o += al(n_grp * 4);
+  L.gact_ok = (int*)(sm + o);
+  o += al(n_grp * 4);
   L.grp_v = (int*)(sm + o);
   o += al(n_grp * 4);
   L.grp_U = (Dsum*)(sm + o);
@@ -136,6 +148,19 @@ __device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, l
     Dsum d = A::dzero();
     for (int m = gr.m0; m < gr.m1; ++m) A::dadd(d, L.mem_u[m]);
     L.grp_U[g] = d;
+  }
+  for (int g = P.n_grp_diag + threadIdx.x; g < ng; g += nt) {
+    const KGroup gr = P.grp[g];
+    int n = 0, okall = 1;
+    for (int m = gr.m0; m < gr.m1; ++m)
+      if (A::nz(L.mem_u[m])) {
+        L.gact_u[gr.m0 + n] = L.mem_u[m];
+        L.gact_src[gr.m0 + n] = L.mem_src[m];
+        okall &= L.mem_ok[m];
+        ++n;
+      }
+    L.gact_n[g] = n;
+    L.gact_ok[g] = okall;
   }
   __syncthreads();
 }
@@ -231,19 +256,24 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
       v[s] = tab[vb + low_digit(pk[s], gr.lbit, gr.lwid)];
       ag[s] = A::azero();
     }
+    const int na = L.gact_n[g];
+    const C* __restrict__ gu = L.gact_u + gr.m0;
+    const long long* __restrict__ gs = L.gact_src + gr.m0;
+    if (L.gact_ok[g]) {
+      // every active member's addresses lie inside x: an inadmissible low
+      // digit (v = 0) gathers a finite in-range value scaled by exactly zero
 #pragma unroll(S >= 6 ? 2 : 4)
-    for (int m = gr.m0; m < gr.m1; ++m) {
-      const C u = L.mem_u[m];
-      if (!A::nz(u)) continue;
-      const TX* __restrict__ src = xb + L.mem_src[m];
-      if (L.mem_ok[m]) {
-        // every address of this member lies inside x: an inadmissible low
-        // digit (v = 0) gathers a finite in-range value that is then scaled
-        // by exactly zero
+      for (int j = 0; j < na; ++j) {
+        const C u = gu[j];
+        const TX* __restrict__ src = xb + gs[j];
 #pragma unroll
         for (int s = 0; s < S; ++s)
           if (FULL || ok[s]) A::fma(ag[s], u, __ldg(src + s * NT));
-      } else {
+      }
+    } else {
+      for (int j = 0; j < na; ++j) {
+        const C u = gu[j];
+        const TX* __restrict__ src = xb + gs[j];
 #pragma unroll
         for (int s = 0; s < S; ++s)
           if ((FULL || ok[s]) && A::nz(v[s])) A::fma(ag[s], u, __ldg(src + s * NT));
