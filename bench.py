@@ -43,7 +43,51 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up + timed applies of --workload/--dtype (for ncu); prints one timing line")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(PROFILE_WORKLOADS))
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     return ap.parse_args()
+
+
+def _workload(name):
+    import workloads as W
+    return {
+        "ferrimagnet_chain_n20": lambda: W.ferrimagnet_chain(20),
+        "tavis_cummings_n20_l64": lambda: W.tavis_cummings(20, 64, seed=7),
+        "tavis_cummings_n24_l64": lambda: W.tavis_cummings(24, 64, seed=7),
+        "square_lattice_4x5": lambda: W.square_lattice_xxz(4, 5, seed=4),
+        "heisenberg_ring_n12": lambda: W.heisenberg_ring(12),
+    }[name]()
+
+
+PROFILE_WORKLOADS = {"ferrimagnet_chain_n20", "tavis_cummings_n20_l64", "tavis_cummings_n24_l64",
+                     "square_lattice_4x5", "heisenberg_ring_n12"}
+
+
+def run_profile(args):
+    """Kernel-only run for profilers: the applies of one workload, nothing else."""
+    import torch
+
+    import workloads as W
+    from paper_2606_02169_gb300 import Hamiltonian
+    m = _workload(args.workload)
+    h = Hamiltonian(m.sites, m.terms)
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    x = W.torch_vector(h.D, 3, dtype=dt)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        h.apply(x, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        h.apply(x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"profile": args.workload, "dtype": args.dtype, "D": h.D, "ms_per_apply": ms,
+                      "gstates_s": h.D / ms / 1e6}))
 
 
 def peaks():
@@ -57,7 +101,8 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("apply.cu", "device_common.cuh", "plan.cpp", "hm_internal.h"):
+    for f in ("apply.cu", "apply_kernel.cuh", "apply_launch.cuh", "apply_df64.cu", "apply_f32.cu",
+              "device_common.cuh", "plan.cpp", "hm_internal.h"):
         with open(os.path.join(ROOT, "paper_2606_02169_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -280,7 +325,7 @@ def run_ours(args):
     value = ws * D / (ms_step * 1e-3) / 1e9
     bytes_alg = 16.0 * D
     achieved = bytes_alg / (ms_step * 1e-3) / 1e9
-    traffic = recorded_traffic("k_apply_df64_" + WORKLOAD)
+    traffic = recorded_traffic("apply_f64_" + WORKLOAD)
 
     # end to end through the public API: pinned host x -> device, apply, y -> pinned host
     xh = x.cpu().pin_memory()
@@ -308,7 +353,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_apply<df64> (FP64 storage, FP32-pair arithmetic)",
+                     "kernel": "one FP64 apply = k_split_f64 (FP64 -> float pairs) + k_apply<df64>",
                      "algorithmic_bytes_per_launch": bytes_alg,
                      "algorithmic_bytes_per_state": 16},
         "clocks": clk,
@@ -424,7 +469,9 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
