@@ -87,7 +87,7 @@ enum {
 /* Build a plan (host call; allocates the plan's small device tables on the
  * current device and synchronises). sites[nsites], terms[nterms] are read and
  * copied. Limits: 1 <= nsites <= 64, D = prod d_k < 2^62, each d_k <= 65536.
- * Cost O(N + |terms|) plus O(B) tables for the low-digit block (B <= 4096). */
+ * Cost O(N + |terms|) plus O(B) tables for the low-digit block (B <= 8192). */
 int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
               hm_handle* out);
 

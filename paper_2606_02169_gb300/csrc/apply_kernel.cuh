@@ -2,7 +2,7 @@
 // produced by exactly one thread from gathered inputs x_{F+offset}; x is
 // read-only, so there is no synchronisation on y and no atomics.
 //
-// Index space: the trailing sites form a low block of B <= 4096 states whose
+// Index space: the trailing sites form a low block of B <= 8192 states whose
 // digits are tabulated once per plan (packed words, no division per state);
 // the leading ("high") sites are uniform across a block. A CTA owns whole low
 // blocks. Per block, its threads evaluate in parallel, into shared memory:
@@ -44,6 +44,9 @@ struct Lists {  // per-block uniform values (shared memory)
   int* grp_v;           // [n_grp_diag + n_grp] v row base
   Dsum* grp_U;          // [n_grp_diag] sum of member u (diagonal groups)
   Dsum* du;             // [1] sum of high diagonal channels
+  KChan* dch;           // plan descriptors, copied once per CTA
+  KMember* dmem;
+  KGroup* dgrp;
 };
 
 template <int AR>
@@ -52,7 +55,8 @@ __host__ __device__ inline size_t lists_bytes(int n_hh, int n_mem, int n_grp, in
   using Dsum = typename Ar<AR>::Dsum;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
   return al(64 * 4) + 2 * al(n_hh * sizeof(C)) + 2 * al(n_hh * 8) + al(16) + 2 * al(n_mem * sizeof(C)) +
-         2 * al(n_mem * 8) + al(n_mem * 4) + 3 * al(n_grp * 4) + al(n_grpd * sizeof(Dsum)) + al(sizeof(Dsum));
+         2 * al(n_mem * 8) + al(n_mem * 4) + 3 * al(n_grp * 4) + al(n_grpd * sizeof(Dsum)) + al(sizeof(Dsum)) +
+         al(n_hh * sizeof(KChan)) + al(n_mem * sizeof(KMember)) + al(n_grp * sizeof(KGroup));
 }
 
 template <int AR>
@@ -93,11 +97,45 @@ __device__ inline Lists<AR> carve(unsigned char* sm, int n_hh, int n_mem, int n_
   L.grp_U = (Dsum*)(sm + o);
   o += al(n_grpd * sizeof(Dsum));
   L.du = (Dsum*)(sm + o);
+  o += al(sizeof(Dsum));
+  L.dch = (KChan*)(sm + o);
+  o += al(n_hh * sizeof(KChan));
+  L.dmem = (KMember*)(sm + o);
+  o += al(n_mem * sizeof(KMember));
+  L.dgrp = (KGroup*)(sm + o);
   return L;
 }
 
-// Evaluate the uniform values of low block `blk`. Called by all threads of
-// the CTA; ends with a barrier.
+// Copy the plan's channel, member and group descriptors into shared memory
+// (once per CTA; ends with a barrier).
+template <int AR>
+__device__ __forceinline__ void load_descriptors(const KPlan& P, const Lists<AR>& L) {
+  for (int c = threadIdx.x; c < P.n_hh_diag + P.n_hh; c += blockDim.x) L.dch[c] = P.ch[c];
+  for (int m = threadIdx.x; m < P.n_mem; m += blockDim.x) L.dmem[m] = P.mem[m];
+  for (int g = threadIdx.x; g < P.n_grp_diag + P.n_grp; g += blockDim.x) L.dgrp[g] = P.grp[g];
+  __syncthreads();
+}
+
+// Warp-wide sums in a fixed order (deterministic).
+__device__ __forceinline__ float wsum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ DF wsum(DF v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o));
+    df_add(v, w);
+  }
+  return v;
+}
+
+// Evaluate the uniform values of low block `blk` (descriptors already in
+// shared memory). Called by all threads of the CTA (8 warps); ends with a
+// barrier.
 template <int AR>
 __device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, long long blk, int nvec) {
   using A = Ar<AR>;
@@ -105,11 +143,12 @@ __device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, l
   using Dsum = typename A::Dsum;
   const C* __restrict__ tab = A::tab(P);
   const int nt = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nt >> 5;
   for (int t = threadIdx.x; t < P.nhigh; t += nt) L.hd[t] = (int)((blk / P.sites[t].mh) % P.sites[t].d);
   __syncthreads();
   const int nhh = P.n_hh_diag + P.n_hh;
   for (int c = threadIdx.x; c < nhh; c += nt) {
-    const KChan ch = P.ch[c];
+    const KChan ch = L.dch[c];
     const int ni = L.hd[ch.si];
     const int nj = (ch.kind & CK_SINGLE) ? 0 : L.hd[ch.sj];
     L.hh_c[c] = tab[ch.tab + ni * ch.dj + nj];
@@ -117,50 +156,65 @@ __device__ __forceinline__ void eval_block(const KPlan& P, const Lists<AR>& L, l
   }
   const long long b0 = blk * P.B;
   for (int m = threadIdx.x; m < P.n_mem; m += nt) {
-    const KMember mb = P.mem[m];
+    const KMember mb = L.dmem[m];
     L.mem_u[m] = tab[mb.utab + L.hd[mb.usite]];
     L.mem_src[m] = mb.off * (long long)nvec;
     L.mem_ok[m] = (b0 + mb.off >= 0) && (b0 + mb.off + P.B <= P.D);
   }
   const int ng = P.n_grp_diag + P.n_grp;
   for (int g = threadIdx.x; g < ng; g += nt) {
-    const KGroup gr = P.grp[g];
+    const KGroup gr = L.dgrp[g];
     L.grp_v[g] = gr.vtab + (gr.vstride ? L.hd[gr.vsite] * gr.vstride : 0);
   }
   __syncthreads();
-  // fixed-order sums and the compacted active list (deterministic)
-  if (threadIdx.x == 0) {
+  // warp-parallel reductions and order-preserving compactions
+  if (warp == 0) {
     Dsum d = A::dzero();
-    for (int c = 0; c < P.n_hh_diag; ++c) A::dadd(d, L.hh_c[c]);
-    L.du[0] = d;
-  } else if (threadIdx.x == 32) {
-    int n = 0;
-    for (int c = P.n_hh_diag; c < nhh; ++c)
-      if (A::nz(L.hh_c[c])) {
-        L.act_c[n] = L.hh_c[c];
-        L.act_src[n] = L.hh_src[c];
-        ++n;
+    for (int c = lane; c < P.n_hh_diag; c += 32) A::dadd(d, L.hh_c[c]);
+    d = wsum(d);
+    if (lane == 0) L.du[0] = d;
+  } else if (warp == 1) {
+    int count = 0;
+    for (int base = P.n_hh_diag; base < nhh; base += 32) {
+      const int c = base + lane;
+      const bool act = c < nhh && A::nz(L.hh_c[c]);
+      const unsigned msk = __ballot_sync(0xffffffffu, act);
+      if (act) {
+        const int pos = count + __popc(msk & ((1u << lane) - 1u));
+        L.act_c[pos] = L.hh_c[c];
+        L.act_src[pos] = L.hh_src[c];
       }
-    L.n_act[0] = n;
-  }
-  for (int g = threadIdx.x; g < P.n_grp_diag; g += nt) {
-    const KGroup gr = P.grp[g];
-    Dsum d = A::dzero();
-    for (int m = gr.m0; m < gr.m1; ++m) A::dadd(d, L.mem_u[m]);
-    L.grp_U[g] = d;
-  }
-  for (int g = P.n_grp_diag + threadIdx.x; g < ng; g += nt) {
-    const KGroup gr = P.grp[g];
-    int n = 0, okall = 1;
-    for (int m = gr.m0; m < gr.m1; ++m)
-      if (A::nz(L.mem_u[m])) {
-        L.gact_u[gr.m0 + n] = L.mem_u[m];
-        L.gact_src[gr.m0 + n] = L.mem_src[m];
-        okall &= L.mem_ok[m];
-        ++n;
+      count += __popc(msk);
+    }
+    if (lane == 0) L.n_act[0] = count;
+  } else {
+    for (int g = warp - 2; g < ng; g += nwarp - 2) {
+      const KGroup gr = L.dgrp[g];
+      if (g < P.n_grp_diag) {
+        Dsum d = A::dzero();
+        for (int m = gr.m0 + lane; m < gr.m1; m += 32) A::dadd(d, L.mem_u[m]);
+        d = wsum(d);
+        if (lane == 0) L.grp_U[g] = d;
+      } else {
+        int count = 0, bad = 0;
+        for (int base = gr.m0; base < gr.m1; base += 32) {
+          const int m = base + lane;
+          const bool act = m < gr.m1 && A::nz(L.mem_u[m]);
+          const unsigned msk = __ballot_sync(0xffffffffu, act);
+          bad |= __any_sync(0xffffffffu, act && !L.mem_ok[m]);
+          if (act) {
+            const int pos = gr.m0 + count + __popc(msk & ((1u << lane) - 1u));
+            L.gact_u[pos] = L.mem_u[m];
+            L.gact_src[pos] = L.mem_src[m];
+          }
+          count += __popc(msk);
+        }
+        if (lane == 0) {
+          L.gact_n[g] = count;
+          L.gact_ok[g] = !bad;
+        }
       }
-    L.gact_n[g] = n;
-    L.gact_ok[g] = okall;
+    }
   }
   __syncthreads();
 }
@@ -220,7 +274,7 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
       A::dadd(ds[s], dtab[lo[s]]);
     }
     for (int g = 0; g < P.n_grp_diag; ++g) {
-      const KGroup gr = P.grp[g];
+      const KGroup gr = L.dgrp[g];
       const Dsum U = L.grp_U[g];
       const int vb = L.grp_v[g];
 #pragma unroll
@@ -247,7 +301,7 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
   }
   // ---- factorised high/low hops, grouped by their low factor ----
   for (int g = P.n_grp_diag; g < P.n_grp_diag + P.n_grp; ++g) {
-    const KGroup gr = P.grp[g];
+    const KGroup gr = L.dgrp[g];
     const int vb = L.grp_v[g];
     C v[S];
     Acc ag[S];
@@ -342,6 +396,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
         int nvec, NvDiv nvdiv) {
   extern __shared__ __align__(16) unsigned char sm[];
   const Lists<AR> L = carve<AR>(sm, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
+  load_descriptors<AR>(P, L);
   const ChunkPlan cp = chunk_plan(P.B * nvec, S);
   const int nchunks = cp.count();
   const long long nitems = P.nblk * nchunks;
@@ -399,6 +454,7 @@ k_batch(const KPlan* __restrict__ plans, const BatchArgs A, int nvec, NvDiv nvdi
       __syncthreads();
       inst = ni;
       L = carve<AR>(sm + lists_off, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
+      load_descriptors<AR>(P, L);
     }
     const long long blk = w - A.blk_start[inst];
     eval_block<AR>(P, L, blk, nvec);

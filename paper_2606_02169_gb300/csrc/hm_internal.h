@@ -15,7 +15,7 @@
 namespace hm {
 
 constexpr int kMaxSites = 64;
-constexpr int kLowBlockMax = 4096;  // low-digit block size bound (tables are O(B))
+constexpr int kLowBlockMax = 8192;  // low-digit block size bound (tables are O(B))
 constexpr int kMaxDim = 65536;      // largest local dimension accepted
 constexpr long long kMaxD = (1LL << 62) - 1;
 

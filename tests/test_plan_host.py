@@ -58,13 +58,13 @@ def test_imaginary_factors_with_real_product(capi):
 def test_workload_plans(capi):
     """Split and channel structure of the workload shapes."""
     P = capi.plan_export(*_m(W.tavis_cummings(24, 64, seed=7)))
-    assert P["B"] == 4096 and P["nblk"] == 2 ** 18 and P["nhigh"] == 18
+    assert P["B"] == 8192 and P["nblk"] == 2 ** 17 and P["nhigh"] == 17
     # boson last: every JC hop of a high spin is factorised into two groups
-    # (a^dag S-: sqrt(n_b); a S+: sqrt(n_b+1)) with 18 members each
+    # (a^dag S-: sqrt(n_b); a S+: sqrt(n_b+1)) with 17 members each
     off = P["grp"][P["n_grp_diag"]:]
-    assert len(off) == 2 and all(g[3] - g[2] == 18 for g in off)
+    assert len(off) == 2 and all(g[3] - g[2] == 17 for g in off)
     P = capi.plan_export(*_m(W.ferrimagnet_chain(20)))
-    assert P["B"] == 3888 and P["hermitian"]
+    assert P["B"] == 7776 and P["hermitian"]
     P = capi.plan_export(*_m(W.heisenberg_ring(12)))
     assert P["B"] == 4096 and P["nblk"] == 1
 
