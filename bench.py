@@ -47,6 +47,8 @@ def parse():
                     help="only warm-up + timed applies of --workload/--dtype (for ncu); prints one timing line")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(PROFILE_WORKLOADS))
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="use the library's default launch shape instead of autotuning it first")
     return ap.parse_args()
 
 
@@ -74,6 +76,7 @@ def run_profile(args):
     m = _workload(args.workload)
     h = Hamiltonian(m.sites, m.terms)
     dt = torch.float64 if args.dtype == "f64" else torch.float32
+    cfg = h.tune(1, dt) if args.tune else None
     x = W.torch_vector(h.D, 3, dtype=dt)
     y = torch.empty_like(x)
     for _ in range(args.warmup):
@@ -87,7 +90,7 @@ def run_profile(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
     print(json.dumps({"profile": args.workload, "dtype": args.dtype, "D": h.D, "ms_per_apply": ms,
-                      "gstates_s": h.D / ms / 1e6}))
+                      "gstates_s": h.D / ms / 1e6, "tuned": cfg}))
 
 
 def peaks():
@@ -311,6 +314,8 @@ def run_ours(args):
     m = W.ferrimagnet_chain(20)
     h = Hamiltonian(m.sites, m.terms)
     D = h.D
+    # launch-shape autotuning is set-up, outside the timed region
+    tuned = h.tune(1, torch.float64) if args.tune else None
     x = W.torch_vector(D, 3 + rank, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
 
@@ -347,7 +352,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "D": D, "nvec": 1,
                    "l2": "inputs larger than L2 (x+y = 968 MB per step), no flush",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+                   "parallelism": "replicas" if ws > 1 else "single GPU", "tuned_launch": tuned},
         "e2e": {"value": e2e_val, "unit": "Gstates/s", "h2d_bytes_per_step": 8 * D,
                 "d2h_bytes_per_step": 8 * D, "steps": k_e2e},
         "gpu_launches": args.steps,
@@ -383,6 +388,8 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     D = h.D
 
     # FP32 storage on the same workload
+    if args.tune:
+        h.tune(1, torch.float32)
     xf = x.float()
     yf = torch.empty_like(xf)
     ms = timed(lambda: h.apply(xf, out=yf), steps, 5, 1, stream) / steps
@@ -410,11 +417,15 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     ht = Hamiltonian(mt.sites, mt.terms)
     Dt = ht.D
     for name, dt, esz in (("tc_1e9_f32", torch.float32, 4), ("tc_1e9_f64", torch.float64, 8)):
+        if args.tune:
+            ht.tune(1, dt)
+            torch.cuda.empty_cache()
         xt = W.torch_vector(Dt, 8, dtype=dt)
         yt = torch.empty_like(xt)
         k = 10
         ms = timed(lambda: ht.apply(xt, out=yt), k, 2, 1, stream) / k
-        out[name] = {"gstates_s": Dt / ms / 1e6, "ms": ms, "hbm_frac_algorithmic": 2 * esz * Dt / ms / 1e6 / hbm}
+        out[name] = {"gstates_s": Dt / ms / 1e6, "ms": ms, "hbm_frac_algorithmic": 2 * esz * Dt / ms / 1e6 / hbm,
+                     "tuned_launch": ht.tuned_config(1, dt)}
         del xt, yt
         torch.cuda.empty_cache()
     del ht

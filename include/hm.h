@@ -107,11 +107,14 @@ int32_t hm_num_terms(hm_handle h);
  * bit-reproducible run to run. */
 int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream);
 
-/* Diagnostic variant of hm_apply. flags bit 0: native FP64 arithmetic for
- * HM_F64 (default: FP64 values split into FP32 pairs, accumulated as a
- * double-float sum with error-free transformations; ~2^-46 relative);
- * bit 1: apply H^T instead of H. ctas > 0 forces the persistent grid size
- * (0 = library default). Same ownership and error rules as hm_apply. */
+/* Diagnostic variant of hm_apply (it ignores hm_tune's choice). flags
+ * bit 0: native FP64 arithmetic for HM_F64 (default: FP64 values split into
+ * FP32 pairs, accumulated as a double-float sum with error-free
+ * transformations; ~2^-46 relative); bit 1: apply H^T instead of H; bit 2:
+ * register-capped kernel variant (one more resident CTA per SM; ignored with
+ * bit 0); bits 8..11: elements per thread, 0 (library choice) or one of
+ * 2, 3, 4, 6, 8, else HM_ERR_INVALID_ARG. ctas > 0 forces the persistent grid
+ * size (0 = library default). Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
 
@@ -169,10 +172,20 @@ int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out);
 int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int64_t nvec,
                    hm_dtype dtype, void* stream);
 
-/* Autotuner: time the apply variants for (nvec, dtype) on scratch vectors and
- * cache the fastest in the plan (and in the process-wide cache keyed by the
- * site-dimension signature). Synchronous. */
+/* Autotuner (no counterpart in the paper; a launch-shape search): time the apply
+ * variants for (nvec, dtype) on scratch vectors it allocates and frees --
+ * elements per thread x register cap x persistent grid size -- and cache the
+ * fastest in the plan, and in a process-wide cache keyed by the site
+ * dimensions and channel counts, for hm_apply, hm_apply_adjoint (gx) and
+ * hm_lanczos. Synchronous; every candidate computes the same y bit for bit
+ * except for the order of the diagonal sums, which no candidate changes. */
 int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
+
+/* The launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
+ * out[1] = elements per thread, out[2] = register-cap variant (int32_t[3],
+ * host; 0 each = library default). No counterpart in the paper (a
+ * diagnostic). */
+int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);
 
 /* Diagnostic, host only: run the host half of hm_create (validation,
  * operator expansion, channel merging, high/low split, tables) without

@@ -34,7 +34,7 @@ HM_LANCZOS_BREAKDOWN = 1
 EXPORTS = [
     "hm_create", "hm_set_coefficients", "hm_dim", "hm_num_terms", "hm_apply", "hm_apply_ex",
     "hm_apply_adjoint", "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune",
-    "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export", "hm_coupling_gradients_static",
+    "hm_tuned_config", "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export", "hm_coupling_gradients_static",
 ]
 
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
     lib.hm_batch_create.argtypes = [ctypes.POINTER(H), i32, ctypes.POINTER(H)]
     lib.hm_batch_apply.argtypes = [H, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, ctypes.c_int, vp]
     lib.hm_tune.argtypes = [H, i64, ctypes.c_int, vp]
+    lib.hm_tuned_config.argtypes = [H, i64, ctypes.c_int, ctypes.POINTER(i32)]
     lib.hm_destroy.argtypes = [H]
     lib.hm_plan_export.argtypes = [ctypes.POINTER(hm_site), i32, ctypes.POINTER(hm_term), i32, i32,
                                    ctypes.c_char_p, i64, ctypes.POINTER(i64)]
@@ -95,7 +96,8 @@ def load(path: str = LIB_PATH):
     lib.hm_strerror.restype = ctypes.c_char_p
     lib.hm_last_error.restype = ctypes.c_char_p
     for name in ("hm_create", "hm_set_coefficients", "hm_apply", "hm_apply_ex", "hm_apply_adjoint",
-                 "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune", "hm_destroy"):
+                 "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune", "hm_tuned_config",
+                 "hm_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

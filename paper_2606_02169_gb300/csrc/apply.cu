@@ -10,7 +10,7 @@
 namespace hm {
 
 template <int AR>
-cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, int ctas);
+cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
 template <int AR>
 cudaError_t launch_batch_t(const KPlan* dplans, const std::vector<const Plan*>& members, const void* const* xs,
                            void* const* ys, long long nvec, cudaStream_t st);
@@ -82,26 +82,26 @@ cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
 
 // y = H x (or H^T x for the transposed KPlan) on stream s
 int apply_on(Plan* p, const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
-             int ctas, bool native_f64) {
+             TuneCfg cfg, bool native_f64) {
   cudaError_t e;
   if (dt == HM_F32) {
-    e = launch_apply_t<AR_F32>(k, x, y, nvec, s, ctas);
+    e = launch_apply_t<AR_F32>(k, x, y, nvec, s, cfg);
   } else if (native_f64) {
-    e = launch_apply_t<AR_F64>(k, x, y, nvec, s, ctas);
+    e = launch_apply_t<AR_F64>(k, x, y, nvec, s, cfg);
   } else {
     int rc = HM_OK;
     const long long n = p->D * nvec;
     void* xs = split_buffer(p, (size_t)n * sizeof(float2), s, &rc);
     if (!xs) return rc;
     e = split_into(x, xs, n, s);
-    if (e == cudaSuccess) e = launch_apply_t<AR_DF64>(k, xs, y, nvec, s, ctas);
+    if (e == cudaSuccess) e = launch_apply_t<AR_DF64>(k, xs, y, nvec, s, cfg);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   return HM_OK;
 }
 
-int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, int ctas) {
-  return apply_on(p, p->k, x, y, nvec, dt, s, ctas, false);
+int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, TuneCfg cfg) {
+  return apply_on(p, p->k, x, y, nvec, dt, s, cfg, false);
 }
 
 int batch_setup(Plan* b) {

@@ -387,11 +387,13 @@ __device__ __forceinline__ void apply_item(const KPlan& P, const Lists<AR>& L, c
   }
 }
 
-template <int AR> struct MinBlocks { static constexpr int v = 2; };
-template <> struct MinBlocks<AR_F32> { static constexpr int v = 4; };
+// Resident CTAs per SM the register allocation must allow: default (MBV = 0)
+// or one more (MBV = 1, fewer registers per thread); the autotuner picks.
+template <int AR, int MBV> struct MinBlocks { static constexpr int v = 2 + MBV; };
+template <int MBV> struct MinBlocks<AR_F32, MBV> { static constexpr int v = 4 + MBV; };
 
-template <int AR, int S, bool NV1>
-__global__ void __launch_bounds__(kNT, MinBlocks<AR>::v)
+template <int AR, int S, bool NV1, int MBV>
+__global__ void __launch_bounds__(kNT, MinBlocks<AR, MBV>::v)
 k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>::TY* __restrict__ y,
         int nvec, NvDiv nvdiv) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -436,7 +438,7 @@ struct BatchArgs {
 };
 
 template <int AR, int S, bool NV1>
-__global__ void __launch_bounds__(kNT, MinBlocks<AR>::v)
+__global__ void __launch_bounds__(kNT, MinBlocks<AR, 0>::v)
 k_batch(const KPlan* __restrict__ plans, const BatchArgs A, int nvec, NvDiv nvdiv, size_t lists_off) {
   extern __shared__ __align__(16) unsigned char sm[];
   KPlan& P = *reinterpret_cast<KPlan*>(sm);

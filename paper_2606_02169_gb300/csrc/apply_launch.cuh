@@ -48,7 +48,7 @@ inline NvDiv make_nvdiv(long long nvec) {
 
 int num_sms();
 
-template <int AR, int S, bool NV1>
+template <int AR, int S, bool NV1, int MBV>
 static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long nvec, int nchunks, cudaStream_t st,
                              int ctas) {
   using TX = typename Ar<AR>::TX;
@@ -56,38 +56,48 @@ static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long n
   const size_t smem = lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag);
   static size_t attr_set = 0;
   if (smem > 48 * 1024 && smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<AR, S, NV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_apply<AR, S, NV1, MBV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
   long long grid = ctas;
   if (grid <= 0) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<AR, S, NV1>, kNT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<AR, S, NV1, MBV>, kNT, smem);
     grid = (long long)num_sms() * std::max(1, occ);
   }
   const long long items = k.nblk * nchunks;
   grid = std::max<long long>(1, std::min(grid, items));
-  k_apply<AR, S, NV1><<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec));
+  k_apply<AR, S, NV1, MBV><<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec));
   return cudaGetLastError();
 }
 
 template <int AR, int S>
 static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
-                                cudaStream_t st, int ctas) {
-  if (nvec == 1) return launch_nv<AR, S, true>(k, x, y, nvec, nchunks, st, ctas);
-  return launch_nv<AR, S, false>(k, x, y, nvec, nchunks, st, ctas);
+                                cudaStream_t st, TuneCfg cfg) {
+  if constexpr (AR != AR_F64) {
+    if (cfg.mb) {
+      if (nvec == 1) return launch_nv<AR, S, true, 1>(k, x, y, nvec, nchunks, st, cfg.ctas);
+      return launch_nv<AR, S, false, 1>(k, x, y, nvec, nchunks, st, cfg.ctas);
+    }
+  }
+  if (nvec == 1) return launch_nv<AR, S, true, 0>(k, x, y, nvec, nchunks, st, cfg.ctas);
+  return launch_nv<AR, S, false, 0>(k, x, y, nvec, nchunks, st, cfg.ctas);
 }
 
+// Elements-per-thread values the kernels are instantiated for.
+constexpr int kShapes[] = {2, 3, 4, 6, 8};
+
 template <int AR>
-cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, int ctas) {
-  const Shape sh = pick_shape((long long)k.B * nvec);
+cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg) {
+  Shape sh = pick_shape((long long)k.B * nvec);
+  if (cfg.s) sh = {cfg.s, chunk_plan((int)(k.B * nvec), cfg.s).count()};
   switch (sh.s) {
-    case 8: return launch_shape<AR, 8>(k, x, y, nvec, sh.nchunks, st, ctas);
-    case 6: return launch_shape<AR, 6>(k, x, y, nvec, sh.nchunks, st, ctas);
-    case 4: return launch_shape<AR, 4>(k, x, y, nvec, sh.nchunks, st, ctas);
-    case 3: return launch_shape<AR, 3>(k, x, y, nvec, sh.nchunks, st, ctas);
-    default: return launch_shape<AR, 2>(k, x, y, nvec, sh.nchunks, st, ctas);
+    case 8: return launch_shape<AR, 8>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 6: return launch_shape<AR, 6>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 4: return launch_shape<AR, 4>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 3: return launch_shape<AR, 3>(k, x, y, nvec, sh.nchunks, st, cfg);
+    default: return launch_shape<AR, 2>(k, x, y, nvec, sh.nchunks, st, cfg);
   }
 }
 

@@ -54,13 +54,24 @@ int check_vec_args(const Plan* p, const void* x, const void* y, long long nvec, 
 }
 
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tune_cache;
+static std::map<std::string, TuneCfg> g_tune_cache;
 
 static std::string tune_signature(const Plan* p, hm_dtype dt, long long nvec) {
   std::string s = std::to_string((int)dt) + "/" + std::to_string(nvec) + "/";
   for (auto& st : p->sites) s += std::to_string(st.dim) + ",";
   s += "/" + std::to_string(p->k.n_hh) + "," + std::to_string(p->k.n_grp) + "," + std::to_string(p->k.n_mem) + "," + std::to_string(p->k.ell_w);
   return s;
+}
+
+TuneCfg tuned_cfg(Plan* p, hm_dtype dt, long long nvec) {
+  auto it = p->tuned.find({(int)dt, nvec});
+  if (it != p->tuned.end()) return it->second;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  if (g_tune_cache.empty()) return TuneCfg{};
+  auto jt = g_tune_cache.find(tune_signature(p, dt, nvec));
+  if (jt == g_tune_cache.end()) return TuneCfg{};
+  p->tuned[{(int)dt, nvec}] = jt->second;
+  return jt->second;
 }
 
 }  // namespace hm
@@ -128,13 +139,7 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
   Plan* p = as_plan(h);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
-  auto it = p->tuned.find({(int)dtype, (long long)nvec});
-  if (it == p->tuned.end() && !g_tune_cache.empty()) {
-    std::lock_guard<std::mutex> g(g_tune_mu);
-    auto jt = g_tune_cache.find(tune_signature(p, dtype, nvec));
-    if (jt != g_tune_cache.end()) it = p->tuned.emplace(std::make_pair((int)dtype, (long long)nvec), jt->second).first;
-  }
-  return launch_apply(p, x, y, nvec, dtype, (cudaStream_t)stream, it == p->tuned.end() ? 0 : it->second);
+  return launch_apply(p, x, y, nvec, dtype, (cudaStream_t)stream, tuned_cfg(p, dtype, nvec));
 }
 
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
@@ -142,8 +147,16 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
   Plan* p = as_plan(h);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
+  TuneCfg cfg;
+  cfg.ctas = ctas > 0 ? ctas : 0;
+  cfg.mb = (flags >> 2) & 1;
+  cfg.s = (flags >> 8) & 15;
+  if (cfg.s && cfg.s != 2 && cfg.s != 3 && cfg.s != 4 && cfg.s != 6 && cfg.s != 8) {
+    set_error("elements per thread must be 0 (default), 2, 3, 4, 6 or 8");
+    return HM_ERR_INVALID_ARG;
+  }
   const KPlan& k = (flags & 2) ? p->kt : p->k;
-  return apply_on(p, k, x, y, nvec, dtype, (cudaStream_t)stream, ctas, (flags & 1) != 0);
+  return apply_on(p, k, x, y, nvec, dtype, (cudaStream_t)stream, cfg, (flags & 1) != 0);
 }
 
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
@@ -238,9 +251,13 @@ int hm_destroy(hm_handle h) {
   return HM_OK;
 }
 
-// Autotuner: time the apply over a ladder of grid sizes (persistent grids of
-// 1..16 CTAs per SM) on scratch vectors and keep the fastest per (dtype, nvec),
-// also in a process-wide cache keyed by the site dimensions and channel counts.
+// Autotuner: time the apply variants on scratch vectors -- elements per
+// thread S in {2, 3, 4, 6, 8} x register cap (default, or one more resident
+// CTA per SM) at the occupancy-sized persistent grid, then the grid ladder
+// (1..16 CTAs per SM) for the best of those -- and keep the fastest per
+// (dtype, nvec), also in a process-wide cache keyed by the site dimensions
+// and channel counts. Each candidate: one untimed launch, then the minimum of
+// three event-timed launches.
 int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
   if (!p || p->is_batch || nvec < 1 || (dtype != HM_F64 && dtype != HM_F32)) {
@@ -267,33 +284,63 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_ctas = 0;
-  const int sms = num_sms();
   int rc = HM_OK;
-  for (int per : {1, 2, 4, 8, 16}) {
-    const int ctas = sms * per;
+  auto time_cfg = [&](TuneCfg c) {
     float tmin = 1e30f;
     for (int rep = 0; rep < 4 && rc == HM_OK; ++rep) {
       cudaEventRecord(e0, s);
-      rc = launch_apply(p, x, y, nvec, dtype, s, ctas);
+      rc = launch_apply(p, x, y, nvec, dtype, s, c);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = HM_ERR_CUDA;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) tmin = std::min(tmin, ms);
     }
+    return tmin;
+  };
+  TuneCfg best{};
+  float tbest = time_cfg(best);
+  for (int sh : {2, 3, 4, 6, 8}) {
+    for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
+      TuneCfg c;
+      c.s = sh;
+      c.mb = mb;
+      const float t = time_cfg(c);
+      if (t < tbest) { tbest = t; best = c; }
+    }
+  }
+  const int sms = num_sms();
+  for (int per : {1, 2, 4, 8, 16}) {
     if (rc != HM_OK) break;
-    if (tmin < best) { best = tmin; best_ctas = ctas; }
+    TuneCfg c = best;
+    c.ctas = sms * per;
+    const float t = time_cfg(c);
+    if (t < tbest) { tbest = t; best = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(x);
   cudaFree(y);
   if (rc != HM_OK) return rc;
-  p->tuned[{(int)dtype, (long long)nvec}] = best_ctas;
+  p->tuned[{(int)dtype, (long long)nvec}] = best;
   std::lock_guard<std::mutex> g(g_tune_mu);
-  g_tune_cache[sig] = best_ctas;
+  g_tune_cache[sig] = best;
+  return HM_OK;
+}
+
+/* Launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
+ * out[1] = elements per thread, out[2] = register-cap variant (0 each =
+ * library default). */
+int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out) {
+  Plan* p = as_plan(h);
+  if (!p || p->is_batch || !out) {
+    set_error("invalid arguments");
+    return HM_ERR_INVALID_ARG;
+  }
+  const TuneCfg c = tuned_cfg(p, dtype, nvec);
+  out[0] = c.ctas;
+  out[1] = c.s;
+  out[2] = c.mb;
   return HM_OK;
 }
 

@@ -112,6 +112,13 @@ struct KPlan {
   const float* ttab_f;
 };
 
+// Launch choice of the apply kernel; 0 = library default for each field.
+struct TuneCfg {
+  int ctas = 0;  // persistent grid size
+  int s = 0;     // elements per thread (rows of a chunk)
+  int mb = 0;    // 1: register cap for one more resident CTA per SM
+};
+
 struct Channel {            // host-side merged channel
   int i = -1, j = -1;       // j = -1: single-site
   int qi = 0, qj = 0;       // n_target = n_source + q
@@ -148,8 +155,8 @@ struct Plan {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
 
-  // autotuned grid size per (dtype, nvec); absent = default
-  std::map<std::pair<int, long long>, int> tuned;
+  // autotuned launch choice per (dtype, nvec); absent = default
+  std::map<std::pair<int, long long>, TuneCfg> tuned;
 
   // batch handle
   bool is_batch = false;
@@ -169,10 +176,10 @@ void set_error(const std::string& s);
 int cuda_fail(cudaError_t e, const char* what);
 
 // kernels (apply.cu / adjoint.cu / lanczos.cu / batch.cu)
-int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
-                 int ctas_override);
+int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, TuneCfg cfg);
 int apply_on(Plan* p, const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
-             int ctas, bool native_f64);
+             TuneCfg cfg, bool native_f64);
+TuneCfg tuned_cfg(Plan* p, hm_dtype dt, long long nvec);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
 int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,

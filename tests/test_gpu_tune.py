@@ -1,0 +1,87 @@
+"""Launch variants the autotuner chooses between (elements per thread S,
+register cap, grid size): each one matches the oracle, and all of them give
+the same y bit for bit, so tuning never changes a result."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import TOL_F32, TOL_F64, abs_bound, check_close, ham, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [2, 3, 4, 6, 8]
+
+MODELS = [
+    ((3, 2, 5, 2, 3, 4, 2, 3, 2), None),                 # ragged low block, 1 high site
+    ((2,) * 14, None),                                     # 2 high sites
+    ((3, 5, 2, 7, 3, 2, 2, 3), ["spin", "boson", "spin", "boson", "spin", "spin", "spin", "spin"]),
+]
+
+
+def _to(torch, a, dtype):
+    return torch.from_numpy(a).to("cuda", torch.float64 if dtype == np.float64 else torch.float32)
+
+
+@pytest.mark.parametrize("dims,kinds", MODELS)
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_every_variant_matches_oracle_and_each_other(dims, kinds, dtype, nvec):
+    torch = torch_cuda()
+    m = W.random_model(list(dims), kinds, nterms=28, seed=11)
+    D = oracle.dimension(m.sites)
+    x = W.vector(D, 12, nvec=nvec)
+    if dtype == np.float32:
+        x = x.astype(np.float32).astype(np.float64)
+    ref = oracle.apply(m.sites, m.terms, x, nvec=nvec)
+    scale = abs_bound(m, x)
+    h = ham(m)
+    xd = _to(torch, x, dtype)
+    base = h.apply_ex(xd)
+    torch.cuda.synchronize()
+    base_np = base.double().cpu().numpy()
+    check_close(base_np, ref, scale, TOL_F64 if dtype == np.float64 else TOL_F32, "default launch")
+    for s in SHAPES:
+        for mb in (False, True):
+            for ctas in (0, 7):
+                y = h.apply_ex(xd, s=s, mb=mb, ctas=ctas)
+                torch.cuda.synchronize()
+                assert torch.equal(y, base), f"S={s} mb={mb} ctas={ctas} differs from the default launch"
+
+
+def test_invalid_elements_per_thread_is_rejected():
+    torch = torch_cuda()
+    m = W.heisenberg_ring(6)
+    h = ham(m)
+    x = torch.zeros(h.D, dtype=torch.float64, device="cuda")
+    for bad in (1, 5, 7, 9, 15):
+        with pytest.raises(RuntimeError):
+            h.apply_ex(x, s=bad)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_tuned_apply_matches_default(dtype):
+    torch = torch_cuda()
+    m = W.ferrimagnet_chain(10)
+    D = oracle.dimension(m.sites)
+    x = W.vector(D, 4)
+    h = ham(m)
+    xd = _to(torch, x, dtype)
+    y0 = h.apply(xd)
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    cfg = h.tune(1, tdt)
+    assert cfg == h.tuned_config(1, tdt)
+    assert cfg["s"] in [0] + SHAPES and cfg["mb"] in (0, 1) and cfg["ctas"] >= 0
+    y1 = h.apply(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    # a second plan with the same signature takes the cached choice without timing
+    h2 = ham(m)
+    assert h2.tuned_config(1, tdt) == cfg
+    gx, _ = h.adjoint(xd, want_gcoef=False)
+    torch.cuda.synchronize()
+    ref = oracle.apply(m.sites, m.terms, x)
+    check_close(y1.double().cpu().numpy(), ref, abs_bound(m, x), TOL_F64 if dtype == np.float64 else TOL_F32,
+                "tuned")
+    # ferrimagnet chain: real symmetric, so H^T gy = H gy
+    assert torch.equal(gx, y1)
