@@ -47,6 +47,8 @@ def parse():
                     help="only warm-up + timed applies of --workload/--dtype (for ncu); prints one timing line")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(PROFILE_WORKLOADS))
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "general"],
+                    help="--profile only: force one apply kernel (auto: library or tuned choice)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="use the library's default launch shape instead of autotuning it first")
     return ap.parse_args()
@@ -76,21 +78,27 @@ def run_profile(args):
     m = _workload(args.workload)
     h = Hamiltonian(m.sites, m.terms)
     dt = torch.float64 if args.dtype == "f64" else torch.float32
-    cfg = h.tune(1, dt) if args.tune else None
+    cfg = h.tune(1, dt) if args.tune and args.kernel == "auto" else None
     x = W.torch_vector(h.D, 3, dtype=dt)
     y = torch.empty_like(x)
+    if args.kernel == "auto":
+        def step():
+            h.apply(x, out=y)
+    else:
+        def step():
+            h.apply_ex(x, out=y, kernel=args.kernel)
     for _ in range(args.warmup):
-        h.apply(x, out=y)
+        step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        h.apply(x, out=y)
+        step()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
-    print(json.dumps({"profile": args.workload, "dtype": args.dtype, "D": h.D, "ms_per_apply": ms,
-                      "gstates_s": h.D / ms / 1e6, "tuned": cfg}))
+    print(json.dumps({"profile": args.workload, "dtype": args.dtype, "kernel": args.kernel, "D": h.D,
+                      "ms_per_apply": ms, "gstates_s": h.D / ms / 1e6, "tuned": cfg}))
 
 
 def peaks():

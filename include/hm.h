@@ -111,10 +111,14 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
  * bit 0: native FP64 arithmetic for HM_F64 (default: FP64 values split into
  * FP32 pairs, accumulated as a double-float sum with error-free
  * transformations; ~2^-46 relative); bit 1: apply H^T instead of H; bit 2:
- * register-capped kernel variant (one more resident CTA per SM; ignored with
- * bit 0); bits 8..11: elements per thread, 0 (library choice) or one of
- * 2, 3, 4, 6, 8, else HM_ERR_INVALID_ARG. ctas > 0 forces the persistent grid
- * size (0 = library default). Same ownership and error rules as hm_apply. */
+ * register-capped general kernel (one more resident CTA per SM); bit 3: the
+ * leaf-tiled kernel (HM_ERR_UNSUPPORTED if the plan has no tile form for
+ * this nvec); bit 4: the general kernel; bits 8..11: rows per iteration of
+ * the tile kernel (1, 2, 4) or elements per thread of the general kernel
+ * (2, 3, 4, 6, 8), 0 = default, anything else HM_ERR_INVALID_ARG. Without
+ * bits 3/4 the general kernel runs. ctas > 0 forces the persistent grid
+ * size (0 = library default).
+ * Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
 
@@ -173,25 +177,30 @@ int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int6
                    hm_dtype dtype, void* stream);
 
 /* Autotuner (no counterpart in the paper; a launch-shape search): time the apply
- * variants for (nvec, dtype) on scratch vectors it allocates and frees --
- * elements per thread x register cap x persistent grid size -- and cache the
- * fastest in the plan, and in a process-wide cache keyed by the site
- * dimensions and channel counts, for hm_apply, hm_apply_adjoint (gx) and
- * hm_lanczos. Synchronous; every candidate computes the same y bit for bit
- * except for the order of the diagonal sums, which no candidate changes. */
+ * variants for (nvec, dtype) on scratch vectors it allocates and frees -- the
+ * general kernel (elements per thread x register cap) and the tile kernel
+ * (rows per iteration), then the persistent grid size for the best -- and
+ * cache the fastest in the plan, and in a process-wide cache keyed by the
+ * site dimensions and channel counts, for hm_apply, hm_apply_adjoint (gx) and
+ * hm_lanczos. Synchronous. The variants of one kernel compute the same y bit
+ * for bit; the two kernels sum in different orders (both within the FP64 /
+ * FP32 tolerances). */
 int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* The launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
- * out[1] = elements per thread, out[2] = register-cap variant (int32_t[3],
- * host; 0 each = library default). No counterpart in the paper (a
- * diagnostic). */
+ * out[1] = elements per thread (general) or rows per iteration (tile),
+ * out[2] = register-cap variant, out[3] = kernel (1 general, 2 tile)
+ * (int32_t[4], host; 0 each = library default). No counterpart in the paper
+ * (a diagnostic). */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);
 
 /* Diagnostic, host only: run the host half of hm_create (validation,
  * operator expansion, channel merging, high/low split, tables) without
- * touching the GPU, and write the resulting tables as JSON text. which = 0
- * exports H, 1 exports H^T. On success *len = bytes needed including the
- * terminating NUL; the text is written only if buf != NULL and
+ * touching the GPU, and write the resulting tables as JSON text. which
+ * bit 0: H^T instead of H; bit 1: the tile kernel's tables for
+ * nvec = which >> 8 (at least 1; HM_ERR_UNSUPPORTED if there is no tile
+ * form), else the general kernel's. On success *len = bytes needed including
+ * the terminating NUL; the text is written only if buf != NULL and
  * bufsize >= *len. Same error codes as hm_create. */
 int hm_plan_export(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
                    int32_t which, char* buf, int64_t bufsize, int64_t* len);

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhm.so")
-SOURCES = ["capi.cpp", "plan.cpp", "apply.cu", "apply_f32.cu", "apply_df64.cu", "apply_f64.cu", "adjoint.cu",
-           "lanczos.cu", "grad_static.cu"]
+SOURCES = ["capi.cpp", "plan.cpp", "tile_plan.cpp", "apply.cu", "apply_f32.cu", "apply_df64.cu", "apply_f64.cu",
+           "tile_f32.cu", "tile_df64.cu", "adjoint.cu", "lanczos.cu", "grad_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -149,7 +149,7 @@ int launch_term_grad(const Plan* p, const void* gy, const void* x, double* gcoef
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef, long long nvec,
                    hm_dtype dt, cudaStream_t s) {
   if (gx) {
-    int rc = apply_on(p, p->kt, gy, gx, nvec, dt, s, tuned_cfg(p, dt, nvec), false);
+    int rc = apply_on(p, true, gy, gx, nvec, dt, s, tuned_cfg(p, dt, nvec), false);
     if (rc) return rc;
   }
   if (!gcoef) return HM_OK;

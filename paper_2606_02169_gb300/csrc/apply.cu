@@ -14,6 +14,8 @@ cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nve
 template <int AR>
 cudaError_t launch_batch_t(const KPlan* dplans, const std::vector<const Plan*>& members, const void* const* xs,
                            void* const* ys, long long nvec, cudaStream_t st);
+template <int AR>
+cudaError_t launch_tile_t(const KTile& k, const void* x, void* y, cudaStream_t st, TuneCfg cfg);
 
 static int g_nsm = 0;
 int num_sms() {
@@ -80,28 +82,50 @@ cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// y = H x (or H^T x for the transposed KPlan) on stream s
-int apply_on(Plan* p, const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+// y = H x (or H^T x) on stream s. Kernel: cfg.kern = 2 the tile kernel (an
+// autotuner candidate; on the benchmark workloads it executes about twice the
+// general kernel's instructions per state), otherwise the general kernel.
+int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64) {
+  const KPlan& k = transpose ? p->kt : p->k;
+  const KTile* tk = cfg.kern == 2 ? get_tile(p, nvec, transpose, s) : nullptr;
+  if (cfg.kern == 2 && !tk) {
+    set_error("this plan has no tile form for that nvec");
+    return HM_ERR_UNSUPPORTED;
+  }
+  const TuneCfg gcfg = cfg;
   cudaError_t e;
-  if (dt == HM_F32) {
-    e = launch_apply_t<AR_F32>(k, x, y, nvec, s, cfg);
-  } else if (native_f64) {
-    e = launch_apply_t<AR_F64>(k, x, y, nvec, s, cfg);
-  } else {
+  const void* xin = x;
+  if (dt == HM_F64 && !native_f64) {
     int rc = HM_OK;
     const long long n = p->D * nvec;
     void* xs = split_buffer(p, (size_t)n * sizeof(float2), s, &rc);
     if (!xs) return rc;
     e = split_into(x, xs, n, s);
-    if (e == cudaSuccess) e = launch_apply_t<AR_DF64>(k, xs, y, nvec, s, cfg);
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 split launch");
+    xin = xs;
+  }
+  e = cudaErrorInvalidConfiguration;
+  if (tk) {
+    if (dt == HM_F32) e = launch_tile_t<AR_F32>(*tk, xin, y, s, cfg);
+    else if (native_f64) e = launch_tile_t<AR_F64>(*tk, xin, y, s, cfg);
+    else e = launch_tile_t<AR_DF64>(*tk, xin, y, s, cfg);
+    if (e == cudaErrorInvalidConfiguration && cfg.kern == 2) {
+      set_error("tile kernel needs more shared memory than a CTA has");
+      return HM_ERR_UNSUPPORTED;
+    }
+  }
+  if (e == cudaErrorInvalidConfiguration) {
+    if (dt == HM_F32) e = launch_apply_t<AR_F32>(k, xin, y, nvec, s, gcfg);
+    else if (native_f64) e = launch_apply_t<AR_F64>(k, xin, y, nvec, s, gcfg);
+    else e = launch_apply_t<AR_DF64>(k, xin, y, nvec, s, gcfg);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   return HM_OK;
 }
 
 int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, TuneCfg cfg) {
-  return apply_on(p, p->k, x, y, nvec, dt, s, cfg, false);
+  return apply_on(p, false, x, y, nvec, dt, s, cfg, false);
 }
 
 int batch_setup(Plan* b) {

@@ -151,12 +151,22 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
   cfg.ctas = ctas > 0 ? ctas : 0;
   cfg.mb = (flags >> 2) & 1;
   cfg.s = (flags >> 8) & 15;
-  if (cfg.s && cfg.s != 2 && cfg.s != 3 && cfg.s != 4 && cfg.s != 6 && cfg.s != 8) {
+  const bool tile = (flags & 8) != 0, general = (flags & 16) != 0;
+  if (tile && general) {
+    set_error("flags ask for both kernels");
+    return HM_ERR_INVALID_ARG;
+  }
+  cfg.kern = tile ? 2 : (general ? 1 : 0);
+  if (tile && cfg.s && cfg.s != 1 && cfg.s != 2 && cfg.s != 4) {
+    set_error("tile kernel rows per iteration must be 0 (default), 1, 2 or 4");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (!tile && cfg.s && cfg.s != 2 && cfg.s != 3 && cfg.s != 4 && cfg.s != 6 && cfg.s != 8) {
     set_error("elements per thread must be 0 (default), 2, 3, 4, 6 or 8");
     return HM_ERR_INVALID_ARG;
   }
-  const KPlan& k = (flags & 2) ? p->kt : p->k;
-  return apply_on(p, k, x, y, nvec, dtype, (cudaStream_t)stream, cfg, (flags & 1) != 0);
+  if (!tile && cfg.s) cfg.kern = 1;  // an element count names the general kernel
+  return apply_on(p, (flags & 2) != 0, x, y, nvec, dtype, (cudaStream_t)stream, cfg, (flags & 1) != 0);
 }
 
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
@@ -243,6 +253,7 @@ int hm_destroy(hm_handle h) {
   if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
   cudaDeviceSynchronize();
   free_plan_device(p);
+  free_tiles(p);
   if (p->scratch) cudaFree(p->scratch);
   if (p->xsplit) cudaFree(p->xsplit);
   if (p->batch_dev) cudaFree(p->batch_dev);
@@ -251,13 +262,14 @@ int hm_destroy(hm_handle h) {
   return HM_OK;
 }
 
-// Autotuner: time the apply variants on scratch vectors -- elements per
-// thread S in {2, 3, 4, 6, 8} x register cap (default, or one more resident
-// CTA per SM) at the occupancy-sized persistent grid, then the grid ladder
-// (1..16 CTAs per SM) for the best of those -- and keep the fastest per
-// (dtype, nvec), also in a process-wide cache keyed by the site dimensions
-// and channel counts. Each candidate: one untimed launch, then the minimum of
-// three event-timed launches.
+// Autotuner: time the apply variants on scratch vectors -- the general
+// kernel's elements per thread S in {2, 3, 4, 6, 8} x register cap (default,
+// or one more resident CTA per SM) and the tile kernel's rows per iteration
+// {1, 2, 4}, each at its occupancy-sized persistent grid, then the grid
+// ladder (1..16 CTAs per SM) for the best of those -- and keep the fastest
+// per (dtype, nvec), also in a process-wide cache keyed by the site
+// dimensions and channel counts. Each candidate: one untimed launch, then the
+// minimum of three event-timed launches.
 int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
   if (!p || p->is_batch || nvec < 1 || (dtype != HM_F64 && dtype != HM_F32)) {
@@ -299,13 +311,29 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
     return tmin;
   };
   TuneCfg best{};
+  best.kern = 1;
   float tbest = time_cfg(best);
   for (int sh : {2, 3, 4, 6, 8}) {
     for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
       TuneCfg c;
+      c.kern = 1;
       c.s = sh;
       c.mb = mb;
       const float t = time_cfg(c);
+      if (t < tbest) { tbest = t; best = c; }
+    }
+  }
+  if (rc == HM_OK && get_tile(p, nvec, false, s)) {
+    for (int rs : {1, 2, 4}) {
+      if (rc != HM_OK) break;
+      TuneCfg c;
+      c.kern = 2;
+      c.s = rs;
+      const float t = time_cfg(c);
+      if (rc == HM_ERR_UNSUPPORTED) {  // tile kernel cannot launch for this plan
+        rc = HM_OK;
+        break;
+      }
       if (t < tbest) { tbest = t; best = c; }
     }
   }
@@ -328,9 +356,7 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
   return HM_OK;
 }
 
-/* Launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
- * out[1] = elements per thread, out[2] = register-cap variant (0 each =
- * library default). */
+/* Launch choice hm_tune stored for (nvec, dtype); see include/hm.h. */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out) {
   Plan* p = as_plan(h);
   if (!p || p->is_batch || !out) {
@@ -341,6 +367,7 @@ int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out) {
   out[0] = c.ctas;
   out[1] = c.s;
   out[2] = c.mb;
+  out[3] = c.kern;
   return HM_OK;
 }
 

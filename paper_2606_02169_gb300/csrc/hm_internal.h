@@ -112,11 +112,74 @@ struct KPlan {
   const float* ttab_f;
 };
 
+// ---------------------------------------------------------------------------
+// Leaf-tiled form of the same operator (the "tile" kernel). The sites split
+// into high | mid | leaf levels (most to least significant). A state index is
+// k = (b * R + r) * F + f with block b (high digits), row r (mid digits) and
+// leaf index f (leaf digits); with nvec right-hand sides the element index is
+// k * nvec + v and a row holds F * nvec consecutive elements. One thread owns
+// one leaf element f*nvec+v for all rows, so everything that depends on the
+// leaf digits only is a per-thread constant, read once per CTA:
+//   * the leaf part of the diagonal, dF(f);
+//   * the hops between leaf sites ("leaf slots": offset, coefficient);
+//   * the leaf factor v_g(f) of every group g >= 1 (below).
+// Every other channel is a "member" whose coefficient u depends on high and
+// mid digits only, so it is uniform across the CTA for a given (b, r):
+//   y_k += sum_{g} v_g(f) * sum_{members m of g} u_m(b, r) x_{k + off_m}
+// with v_0 = 1. Group g >= 1 collects the channels with one leaf site whose
+// leaf factor (local diagonal of the leaf operator, Sec. IV.B) is v_g; their
+// other site carries u. Zero factors are inadmissible digits (Sec. IV.B step
+// 3): a zero u drops the member for the whole row; a zero v_g(f) redirects the
+// thread's gathers of that group to an in-range element (fix_g) that is then
+// scaled by exactly zero.
+// ---------------------------------------------------------------------------
+struct KTileSite {
+  long long stride;  // high: in blocks; mid: in rows
+  int d;
+  int pad;
+};
+
+struct KTMem {
+  long long off;   // element offset of the source (0 for diagonal members)
+  int tab;         // coefficient table base: tab[n_a * db + n_b] over TARGET digits
+  int db;          // row length (1: single-site table)
+  uint8_t sa, sb;  // sites (index into KTile::sites; sb = 255: none)
+  uint8_t grp;     // group (0: leaf factor 1)
+  uint8_t diag;    // source offset 0
+};
+static_assert(sizeof(KTMem) == 24, "KTMem layout");
+
+struct KTile {
+  long long D;          // states
+  long long nblk;       // blocks of R rows x F leaf states
+  int F, R;             // leaf states per row, rows per block
+  int nvec;             // right-hand sides the element offsets were built for
+  int nt;               // threads per CTA: F * nvec rounded up to a warp
+  int nhigh, nmid;      // sites [0, nhigh) high, [nhigh, nhigh + nmid) mid
+  int G;                // groups including group 0
+  int n_bmem, n_rmem;   // members on high sites only | with a mid site
+  int fs_w;             // leaf-slot width (max over f)
+  const KTileSite* sites;   // [nhigh + nmid]
+  const KTMem* bmem;        // [n_bmem] sorted by group
+  const KTMem* rmem;        // [n_rmem] sorted by group
+  const int* bgrp;          // [G + 1] member ranges of bmem per group
+  const int* rgrp;          // [G + 1] member ranges of rmem per group
+  const double* tab;        // member coefficient tables
+  // per-leaf-state tables (F entries each), one copy per arithmetic
+  const double* dF_d; const float2* dF_df; const float* dF_f;
+  const double* v_d;  const float2* v_df;  const float* v_f;   // [(G-1) * F]
+  const int* fix;           // [(G-1) * F] element offset added when v = 0
+  const int* fs_n;          // [F] leaf slots of each leaf state
+  const int* fs_off;        // [fs_w * F] element offsets
+  const double* fs_d; const float2* fs_df; const float* fs_f;  // [fs_w * F]
+};
+
 // Launch choice of the apply kernel; 0 = library default for each field.
 struct TuneCfg {
   int ctas = 0;  // persistent grid size
   int s = 0;     // elements per thread (rows of a chunk)
   int mb = 0;    // 1: register cap for one more resident CTA per SM
+  int kern = 0;  // 0: library choice, 1: general kernel, 2: tile kernel
 };
 
 struct Channel {            // host-side merged channel
@@ -155,6 +218,19 @@ struct Plan {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
 
+  // merged channels of H and H^T (H^T empty when H is symmetric) and the
+  // identity part, kept for building tile tables per nvec
+  std::vector<Channel> chH, chT;
+  double constant = 0.0;
+  // tile tables per (nvec, transpose); device memory owned here. A plan whose
+  // shape has no tile form records that with ok = false.
+  struct TileSet {
+    bool ok = false;
+    KTile k{};
+    void* dev = nullptr;
+  };
+  std::map<std::pair<long long, int>, TileSet> tiles;
+
   // autotuned launch choice per (dtype, nvec); absent = default
   std::map<std::pair<int, long long>, TuneCfg> tuned;
 
@@ -169,6 +245,17 @@ struct Plan {
 // plan.cpp
 int build_plan(Plan* p);            // (re)derive tables from sites/terms and upload
 void free_plan_device(Plan* p);
+
+// tile_plan.cpp
+struct HostTile;
+int derive_tile(const Plan* p, const std::vector<Channel>& ch, double constant, long long nvec, HostTile& out);
+// tile tables for (nvec, transpose), built and uploaded on first use; NULL
+// when the plan has no tile form (or cannot be built right now, e.g. during
+// stream capture)
+const KTile* get_tile(Plan* p, long long nvec, bool transpose, cudaStream_t s);
+void free_tiles(Plan* p);
+std::string export_tile_json(const Plan* p, const std::vector<Channel>& ch, double constant, long long nvec,
+                             int* rc);
 int plan_check(const Plan* p);
 
 // error text (capi.cpp)
@@ -177,7 +264,7 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // kernels (apply.cu / adjoint.cu / lanczos.cu / batch.cu)
 int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, TuneCfg cfg);
-int apply_on(Plan* p, const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64);
 TuneCfg tuned_cfg(Plan* p, hm_dtype dt, long long nvec);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,

@@ -229,7 +229,7 @@ static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, do
     cudaMemsetAsync(vp, 0, sizeof(T) * n, s);
     for (int k = 0; k < m; ++k) {
       if (psi) k_axpy<T><<<vb, 256, 0, s>>>(psi, vk, (*u)[k], n);
-      int arc = apply_on(p, p->k, vk, w, 1, dt, s, tuned_cfg(p, dt, 1), false);
+      int arc = apply_on(p, false, vk, w, 1, dt, s, tuned_cfg(p, dt, 1), false);
       if (arc) return arc;
       dot(vk, w, dal + k, 0);
       k_axpy2<T><<<vb, 256, 0, s>>>(w, vk, k > 0 ? vp : nullptr, dal + k, k > 0 ? dbe + k - 1 : nullptr, n);

@@ -584,6 +584,9 @@ int derive_plan(Plan* p, HostPlanData& out) {
     for (auto& c : dv.ch) tr.push_back(transpose_channel(c));
     build_tables(p, tr, dv.constant, ptab, ks, Ht);
   }
+  p->chH = dv.ch;
+  p->chT = tr;
+  p->constant = dv.constant.real();
 
   // per-term channels (adjoint gradients): full-digit lookups, unit coefficients
   for (size_t c = 0; c < dv.tch.size(); ++c) {
@@ -697,6 +700,7 @@ int build_plan(Plan* p) {
     if (sc.bytes) std::memcpy(host.data() + sc.off, sc.src, sc.bytes);
 
   free_plan_device(p);
+  free_tiles(p);
   cudaError_t e = cudaMalloc(&p->dev, total);
   if (e != cudaSuccess) {
     p->dev = nullptr;
@@ -778,6 +782,12 @@ int export_plan(Plan* p, int which, std::string& o) {
   HostPlanData hd;
   int rc = derive_plan(p, hd);
   if (rc) return rc;
+  if (which & 2) {  // tile tables for nvec = which >> 8 (at least 1)
+    const bool tr = (which & 1) && !p->hermitian;
+    const long long nvec = std::max(1, which >> 8);
+    o = export_tile_json(p, tr ? p->chT : p->chH, p->constant, nvec, &rc);
+    return rc;
+  }
   const HostTables& H = (which == 1 && !p->hermitian) ? hd.Ht : hd.Hf;
   auto I = [&](long long v) { o += std::to_string(v); };
   o = "{";

@@ -103,12 +103,16 @@ class Hamiltonian:
                                    _stream(stream)), "hm_apply")
         return y
 
-    def apply_ex(self, x, out=None, native_f64=False, transpose=False, ctas=0, s=0, mb=False, stream=None):
-        """hm_apply with an explicit launch choice: s elements per thread (0 =
-        library choice), mb = register-capped variant, ctas = grid size."""
+    def apply_ex(self, x, out=None, native_f64=False, transpose=False, ctas=0, s=0, mb=False, kernel=None,
+                 stream=None):
+        """hm_apply with an explicit launch choice. kernel: None (library
+        choice), "tile" or "general". s: rows per iteration of the tile kernel
+        (1, 2, 4) or elements per thread of the general one (2, 3, 4, 6, 8);
+        0 = default. mb: register-capped general kernel. ctas: grid size."""
         _check_vec(x, "x")
         y = torch.empty_like(x) if out is None else out
-        flags = (1 if native_f64 else 0) | (2 if transpose else 0) | (4 if mb else 0) | (int(s) << 8)
+        kf = {None: 0, "tile": 8, "general": 16}[kernel]
+        flags = (1 if native_f64 else 0) | (2 if transpose else 0) | (4 if mb else 0) | kf | (int(s) << 8)
         C.check(self._lib.hm_apply_ex(self._h, x.data_ptr(), y.data_ptr(), self._nvec(x), _dtype_code(x),
                                       flags, int(ctas), _stream(stream)), "hm_apply_ex")
         return y
@@ -156,11 +160,12 @@ class Hamiltonian:
         return self.tuned_config(nvec, dtype)
 
     def tuned_config(self, nvec: int = 1, dtype=torch.float64):
-        """dict(ctas, s, mb) of the stored launch choice (0 = library default)."""
+        """dict(ctas, s, mb, kernel) of the stored launch choice (0 = library
+        default; kernel 1 = general, 2 = tile)."""
         code = C.HM_F64 if dtype == torch.float64 else C.HM_F32
-        out = (ctypes.c_int32 * 3)()
+        out = (ctypes.c_int32 * 4)()
         C.check(self._lib.hm_tuned_config(self._h, int(nvec), code, out), "hm_tuned_config")
-        return {"ctas": out[0], "s": out[1], "mb": out[2]}
+        return {"ctas": out[0], "s": out[1], "mb": out[2], "kernel": out[3]}
 
 
 class Batch:

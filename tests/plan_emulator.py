@@ -66,3 +66,66 @@ def emulate(P, x):
             acc[nz] += cf[nz] * x[src]
         y[base:base + B] = acc
     return y
+
+
+def emulate_tile(T, x):
+    """The tile kernel's algorithm on its exported tables (hm_plan_export with
+    the tile bit): blocks of R rows of F leaf states, per-row uniform members
+    compacted by group, per-leaf-state diagonal, leaf factors and leaf hops.
+    x: D*nvec values, state-major. Asserts that every gather is in range."""
+    F, R, nblk, nvec = T["F"], T["R"], T["nblk"], T["nvec"]
+    nhigh, G = T["nhigh"], T["G"]
+    sites = T["sites"]
+    tab = np.asarray(T["tab"], dtype=np.float64)
+    mems = T["bmem"] + T["rmem"]
+    dF = np.asarray(T["dF"], dtype=np.float64)
+    v = np.asarray(T["v"], dtype=np.float64).reshape(G - 1, F) if G > 1 else np.zeros((0, F))
+    fix = np.asarray(T["fix"], dtype=np.int64).reshape(G - 1, F) if G > 1 else np.zeros((0, F), np.int64)
+    fs_w = T["fs_w"]
+    fs_n = np.asarray(T["fs_n"], dtype=np.int64)
+    fs_off = np.asarray(T["fs_off"], dtype=np.int64).reshape(-1, F)
+    fs = np.asarray(T["fs"], dtype=np.float64).reshape(-1, F)
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    rowE = F * nvec
+    t = np.arange(rowE)
+    f = t // nvec
+    y = np.zeros(n)
+
+    def gather(idx):
+        assert idx.min(initial=0) >= 0 and idx.max(initial=0) < n, "gather out of range"
+        return x[idx]
+
+    for blk in range(nblk):
+        hd = [(blk // sites[s][0]) % sites[s][1] for s in range(nhigh)]
+        for r in range(R):
+            def digit(s):
+                return hd[s] if s < nhigh else (r // sites[s][0]) % sites[s][1]
+            k = (blk * R + r) * rowE + t
+            lists = [[] for _ in range(G)]
+            ud = np.zeros(G)
+            for off, tb, db, sa, sb, g, dg in mems:
+                u = tab[tb + digit(sa) * db + (digit(sb) if sb >= 0 else 0)]
+                if dg:
+                    ud[g] += u
+                elif u != 0.0:
+                    lists[g].append((off, u))
+            xs = gather(k)
+            acc = (ud[0] + dF[f]) * xs
+            for g in range(1, G):
+                acc = acc + v[g - 1][f] * (ud[g] * xs)
+            for off, u in lists[0]:
+                acc = acc + u * gather(k + off)
+            for g in range(1, G):
+                kk = k + fix[g - 1][f]
+                ag = np.zeros(rowE)
+                for off, u in lists[g]:
+                    ag = ag + u * gather(kk + off)
+                acc = acc + v[g - 1][f] * ag
+            for w in range(fs_w):
+                msk = w < fs_n[f]
+                if not msk.any():
+                    continue
+                acc[msk] = acc[msk] + fs[w][f[msk]] * gather(k[msk] + fs_off[w][f[msk]])
+            y[k] = acc
+    return y

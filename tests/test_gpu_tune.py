@@ -11,6 +11,7 @@ from gpu_util import TOL_F32, TOL_F64, abs_bound, check_close, ham, torch_cuda
 pytestmark = pytest.mark.gpu
 
 SHAPES = [2, 3, 4, 6, 8]
+TILE_ROWS = [1, 2, 4]
 
 MODELS = [
     ((3, 2, 5, 2, 3, 4, 2, 3, 2), None),                 # ragged low block, 1 high site
@@ -35,18 +36,19 @@ def test_every_variant_matches_oracle_and_each_other(dims, kinds, dtype, nvec):
         x = x.astype(np.float32).astype(np.float64)
     ref = oracle.apply(m.sites, m.terms, x, nvec=nvec)
     scale = abs_bound(m, x)
+    tol = TOL_F64 if dtype == np.float64 else TOL_F32
     h = ham(m)
     xd = _to(torch, x, dtype)
-    base = h.apply_ex(xd)
-    torch.cuda.synchronize()
-    base_np = base.double().cpu().numpy()
-    check_close(base_np, ref, scale, TOL_F64 if dtype == np.float64 else TOL_F32, "default launch")
-    for s in SHAPES:
-        for mb in (False, True):
-            for ctas in (0, 7):
-                y = h.apply_ex(xd, s=s, mb=mb, ctas=ctas)
-                torch.cuda.synchronize()
-                assert torch.equal(y, base), f"S={s} mb={mb} ctas={ctas} differs from the default launch"
+    for kernel, shapes, mbs in (("general", SHAPES, (False, True)), ("tile", TILE_ROWS, (False,))):
+        base = h.apply_ex(xd, kernel=kernel)
+        torch.cuda.synchronize()
+        check_close(base.double().cpu().numpy(), ref, scale, tol, f"{kernel} default launch")
+        for s in shapes:
+            for mb in mbs:
+                for ctas in (0, 7):
+                    y = h.apply_ex(xd, s=s, mb=mb, ctas=ctas, kernel=kernel)
+                    torch.cuda.synchronize()
+                    assert torch.equal(y, base), f"{kernel} S={s} mb={mb} ctas={ctas} differs from its default"
 
 
 def test_invalid_elements_per_thread_is_rejected():
@@ -60,21 +62,23 @@ def test_invalid_elements_per_thread_is_rejected():
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_tuned_apply_matches_default(dtype):
+def test_tuned_apply_matches_its_kernel(dtype):
     torch = torch_cuda()
     m = W.ferrimagnet_chain(10)
     D = oracle.dimension(m.sites)
     x = W.vector(D, 4)
     h = ham(m)
     xd = _to(torch, x, dtype)
-    y0 = h.apply(xd)
     tdt = torch.float64 if dtype == np.float64 else torch.float32
     cfg = h.tune(1, tdt)
     assert cfg == h.tuned_config(1, tdt)
-    assert cfg["s"] in [0] + SHAPES and cfg["mb"] in (0, 1) and cfg["ctas"] >= 0
+    assert cfg["kernel"] in (1, 2) and cfg["ctas"] >= 0 and cfg["mb"] in (0, 1)
+    assert cfg["s"] in ([0] + SHAPES if cfg["kernel"] == 1 else [0] + TILE_ROWS)
     y1 = h.apply(xd)
+    kernel = "general" if cfg["kernel"] == 1 else "tile"
+    y2 = h.apply_ex(xd, kernel=kernel, s=cfg["s"], mb=bool(cfg["mb"]), ctas=cfg["ctas"])
     torch.cuda.synchronize()
-    assert torch.equal(y0, y1)
+    assert torch.equal(y1, y2)
     # a second plan with the same signature takes the cached choice without timing
     h2 = ham(m)
     assert h2.tuned_config(1, tdt) == cfg
@@ -83,5 +87,5 @@ def test_tuned_apply_matches_default(dtype):
     ref = oracle.apply(m.sites, m.terms, x)
     check_close(y1.double().cpu().numpy(), ref, abs_bound(m, x), TOL_F64 if dtype == np.float64 else TOL_F32,
                 "tuned")
-    # ferrimagnet chain: real symmetric, so H^T gy = H gy
+    # ferrimagnet chain: real symmetric, so H^T gy = H gy with the same tables
     assert torch.equal(gx, y1)

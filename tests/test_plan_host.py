@@ -81,3 +81,56 @@ def test_workload_shapes_small(capi, model):
     P = capi.plan_export(model.sites, model.terms, 0)
     ref = oracle.apply(model.sites, model.terms, x).real
     assert np.linalg.norm(emulate(P, x) - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+# ---- tile form (leaf-tiled kernel) -------------------------------------------------
+
+TILE_CASES = CASES + [
+    ((2,) * 12, None),
+    ((2, 3) * 5, None),
+    ((3,) * 9, None),
+    ((5, 4, 3, 6, 2, 2), None),
+    ((2,) * 6 + (64,), ["spin"] * 6 + ["boson"]),
+]
+
+
+@pytest.mark.parametrize("dims,kinds", TILE_CASES)
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_tile_tables_reproduce_h_and_transpose(capi, dims, kinds, nvec):
+    from plan_emulator import emulate_tile
+    m = W.random_model(list(dims), kinds, nterms=24, seed=5)
+    D = oracle.dimension(m.sites)
+    x = W.vector(D, 9, nvec=nvec)
+    for which in (0, 1):
+        try:
+            T = capi.plan_export(m.sites, m.terms, which | 2 | (nvec << 8))
+        except capi.HmError as e:
+            assert e.code == capi.HM_ERR_UNSUPPORTED
+            continue
+        assert T["F"] * nvec <= 512 and T["nblk"] * T["R"] * T["F"] == D
+        y = emulate_tile(T, x)
+        ref = oracle.apply(m.sites, m.terms, x, nvec=nvec).real if which == 0 else \
+            np.asarray(oracle.dense(m.sites, m.terms, sparse=True).T @ x.reshape(D, nvec)).real.reshape(-1)
+        assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref), (which, T["F"], T["R"])
+
+
+@pytest.mark.parametrize("model", [W.ferrimagnet_chain(12), W.tavis_cummings(6, 8, seed=1),
+                                   W.square_lattice_xxz(3, 4, seed=4), W.heisenberg_ring(13),
+                                   W.xxz_spin1_chain(9, seed=3)])
+def test_tile_workload_shapes(capi, model):
+    from plan_emulator import emulate_tile
+    D = oracle.dimension(model.sites)
+    x = W.vector(D, 4)
+    T = capi.plan_export(model.sites, model.terms, 2 | (1 << 8))
+    ref = oracle.apply(model.sites, model.terms, x).real
+    assert np.linalg.norm(emulate_tile(T, x) - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_tile_split_of_the_benchmark_shapes(capi):
+    T = capi.plan_export(*_m(W.ferrimagnet_chain(20)), 2 | (1 << 8))
+    assert (T["F"], T["R"], T["nt"]) == (216, 36, 224) and T["nblk"] == 7776
+    T = capi.plan_export(*_m(W.tavis_cummings(24, 64, seed=7)), 2 | (1 << 8))
+    assert (T["F"], T["R"], T["nt"]) == (256, 64, 256)
+    # boson last in the leaf: every high or mid spin's JC hop is a member of
+    # one of two leaf-factor groups (sqrt(n_b) and sqrt(n_b + 1))
+    assert T["G"] == 3
