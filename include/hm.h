@@ -168,10 +168,14 @@ int hm_lanczos(hm_handle h, const void* v0, int32_t steps, hm_dtype dtype, int32
                double* alpha, double* beta, int32_t* steps_done, void* psi0_out, double* e0,
                void* stream);
 
-/* Batched apply over many plans of uneven size: one persistent launch walks a
- * (instance, tile) work list. hs[n] stay owned by the caller and must outlive
- * the batch. xs[b], ys[b]: device pointers (arrays of n pointers, host
- * memory). All instances share nvec and dtype. */
+/* Batched apply over many plans of uneven size: one persistent launch per
+ * 128 instances walks an (instance, block[, chunk]) work list; an instance
+ * with enough work to fill the GPU by itself gets a plain apply launch
+ * instead (same results as hm_apply on it). hs[n] stay owned by the caller
+ * and must outlive the batch; each call reads the members' tables as they
+ * are then (a CUDA graph captured before an hm_set_coefficients on a member
+ * must be captured again). xs[b], ys[b]: device pointers (arrays of n
+ * pointers, host memory). All instances share nvec and dtype. */
 int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out);
 int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int64_t nvec,
                    hm_dtype dtype, void* stream);

@@ -4,25 +4,37 @@
 //   g_t = sum_F gy_F (O_t x)_F -- per-term coupling gradients. O_t is term t
 //                   with unit coefficient; its channels follow the same source
 //                   reconstruction as the forward map (Sec. IV.B steps 1-5).
-// g_t is accumulated in FP64 per lane, reduced per warp by shuffles, per CTA
-// through shared memory in warp order, and across CTAs by a second kernel in
-// CTA order: a fixed-order reduction, bit-reproducible for a fixed grid.
+// g_t is accumulated per lane as a double-float sum on the FP32 pipe (GB300
+// runs FP64 FMA at about 1/70 of the FP32 rate): FP64 inputs are split into
+// (hi, lo) float pairs as they are read, the product gy * x is formed from the
+// exact product of the hi parts (Dekker) plus the cross terms, and the
+// coefficient product and the sum use the error-free transformations of
+// device_common.cuh (about 2^-46 relative overall). Lanes are reduced per
+// warp by shuffles in a fixed order, per CTA through shared memory in FP64 in
+// warp order, and across CTAs by a second kernel in CTA order: a fixed-order
+// reduction, bit-reproducible for a fixed grid.
 #include <algorithm>
 
 #include "device_common.cuh"
 
 namespace hm {
 
+// input element as a (hi, lo) float pair
+__device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f); }
+__device__ __forceinline__ float2 as_pair(double v) { return split_f64(v); }
 
-template <class T>
-__device__ __forceinline__ double as_f64(T v);
-template <>
-__device__ __forceinline__ double as_f64<float>(float v) { return f2d_exact(v); }
-template <>
-__device__ __forceinline__ double as_f64<double>(double v) { return v; }
+// product of two float pairs without the lo*lo term: (s, c) with s + c equal
+// to a * b to about 2^-46 relative
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return make_float2(p, e);
+}
 
 constexpr int kGradWarps = 8;
-constexpr int kGradV = 4;
+constexpr int kGradV = 8;
 
 template <class T>
 __global__ void __launch_bounds__(256)
@@ -54,6 +66,7 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
     bool ok[V];
     long long kk[V];
     uint32_t pk[V];
+    float2 g1[V];  // gy of the row (nvec == 1)
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       lo[v] = lo0 + lane + 32 * v;
@@ -61,9 +74,10 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
       if (!ok[v]) lo[v] = 0;
       kk[v] = hb * P.B + lo[v];
       pk[v] = __ldg(P.ptab + lo[v]);
+      g1[v] = (nvec == 1 && ok[v]) ? as_pair(gy[kk[v]]) : make_float2(0.f, 0.f);
     }
     int cur = -1;
-    double acc = 0.0;
+    DF acc{0.f, 0.f};
     for (int c = 0; c <= P.nterm_ch; ++c) {
       const bool last = (c == P.nterm_ch);
       KTermChan ch;
@@ -71,12 +85,16 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
       if (last || ch.term != cur) {
         if (cur >= 0) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == 0) mysm[cur] += acc;
+          for (int o = 16; o > 0; o >>= 1) {
+            const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, acc.s, o),
+                                         __shfl_xor_sync(0xffffffffu, acc.c, o));
+            df_add(acc, w);
+          }
+          if (lane == 0) mysm[cur] += df_to_double(acc);
         }
         if (last) break;
         cur = ch.term;
-        acc = 0.0;
+        acc = DF{0.f, 0.f};
       }
       const KSite si = P.sites[ch.si];
       const bool single = ch.sj == 255;
@@ -88,13 +106,19 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
       for (int v = 0; v < V; ++v) {
         const int ni = si.is_low ? low_digit(pk[v], si.lbit, si.lwid) : hi_i;
         const int nj = single ? 0 : (sj.is_low ? low_digit(pk[v], sj.lbit, sj.lwid) : hi_j);
-        const double cf = P.ttab_d[ch.tab + ni * ch.dj + nj];
-        if (ok[v] && cf != 0.0) {
-          const T* g = gy + kk[v] * nvec;
-          const T* xs = x + (kk[v] + ch.off) * nvec;
-          double s = 0.0;
-          for (long long u = 0; u < nvec; ++u) s = fma(as_f64(g[u]), as_f64(xs[u]), s);
-          acc = fma(cf, s, acc);
+        const float2 cf = P.ttab_df[ch.tab + ni * ch.dj + nj];
+        if (ok[v] && cf.x != 0.0f) {
+          if (nvec == 1) {
+            const float2 t = pair_mul(g1[v], as_pair(x[kk[v] + ch.off]));
+            df_fma(acc, cf, t.x, t.y);
+          } else {
+            const T* g = gy + kk[v] * nvec;
+            const T* xs = x + (kk[v] + ch.off) * nvec;
+            DF s{0.f, 0.f};
+            for (long long u = 0; u < nvec; ++u) df_add(s, pair_mul(as_pair(g[u]), as_pair(xs[u])));
+            const float2 n = df_norm(s);
+            df_fma(acc, cf, n.x, n.y);
+          }
         }
       }
     }

@@ -12,8 +12,8 @@ namespace hm {
 template <int AR>
 cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
 template <int AR>
-cudaError_t launch_batch_t(const KPlan* dplans, const std::vector<const Plan*>& members, const void* const* xs,
-                           void* const* ys, long long nvec, cudaStream_t st);
+cudaError_t launch_batch_t(const std::vector<const Plan*>& members, const void* const* xs, void* const* ys,
+                           long long nvec, cudaStream_t st);
 template <int AR>
 cudaError_t launch_tile_t(const KTile& k, const void* x, void* y, cudaStream_t st, TuneCfg cfg);
 
@@ -128,57 +128,51 @@ int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, c
   return apply_on(p, false, x, y, nvec, dt, s, cfg, false);
 }
 
+// Nothing to upload: each launch carries the members' current plans in its
+// kernel parameters.
 int batch_setup(Plan* b) {
-  const size_t n = b->members.size();
-  std::vector<KPlan> ks(n);
-  b->member_gen.assign(n, 0);
-  for (size_t i = 0; i < n; ++i) {
-    ks[i] = b->members[i]->k;
-    b->member_gen[i] = b->members[i]->gen;
-  }
-  if (!b->batch_dev) {
-    cudaError_t e = cudaMalloc(&b->batch_dev, sizeof(KPlan) * n);
-    if (e != cudaSuccess) {
-      b->batch_dev = nullptr;
-      return cuda_fail(e, "batch plan table");
-    }
-  }
-  cudaError_t e = cudaMemcpy(b->batch_dev, ks.data(), sizeof(KPlan) * n, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "batch plan upload");
+  (void)b;
   return HM_OK;
 }
 
+// Instances with enough work to fill the GPU on their own (at least two
+// chunk items per resident CTA) run as plain launches of the single-plan
+// kernel, whose plan fields are constant-bank operands at fixed offsets; the
+// rest share one persistent work-queue launch, which replaces their
+// under-filled launches.
+static bool fills_gpu(const Plan* p, long long nvec) {
+  const long long items = p->nblk * (((long long)p->B * nvec + 2047) / 2048);
+  return items >= 2LL * 4 * num_sms();
+}
+
 int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec, hm_dtype dt, cudaStream_t s) {
-  bool stale = false;
-  for (size_t i = 0; i < b->members.size(); ++i) stale |= (b->members[i]->gen != b->member_gen[i]);
-  if (stale) {  // a member was re-planned (hm_set_coefficients): refresh its tables
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cs);
-    if (cs != cudaStreamCaptureStatusNone) {
-      set_error("a batch member changed since the batch was built; refresh outside stream capture");
-      return HM_ERR_INVALID_ARG;
+  std::vector<const Plan*> mem;
+  std::vector<const void*> sx;
+  std::vector<void*> sy;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    Plan* p = b->members[i];
+    if (fills_gpu(p, nvec)) {
+      int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, tuned_cfg(p, dt, nvec), false);
+      if (rc) return rc;
+      continue;
     }
-    int rc = batch_setup(b);
-    if (rc) return rc;
-  }
-  std::vector<const Plan*> mem(b->members.begin(), b->members.end());
-  cudaError_t e;
-  if (dt == HM_F32) {
-    e = launch_batch_t<AR_F32>((const KPlan*)b->batch_dev, mem, xs, ys, nvec, s);
-  } else {
-    // each member's FP64 input is split into that member's buffer first
-    std::vector<const void*> sx(mem.size());
-    for (size_t i = 0; i < mem.size(); ++i) {
+    mem.push_back(p);
+    sy.push_back(ys[i]);
+    if (dt == HM_F32) {
+      sx.push_back(xs[i]);
+    } else {
+      // each member's FP64 input is split into that member's buffer first
       int rc = HM_OK;
-      Plan* p = b->members[i];
       void* buf = split_buffer(p, (size_t)(p->D * nvec) * sizeof(float2), s, &rc);
       if (!buf) return rc;
-      e = split_into(xs[i], buf, p->D * nvec, s);
+      cudaError_t e = split_into(xs[i], buf, p->D * nvec, s);
       if (e != cudaSuccess) return cuda_fail(e, "batch split");
-      sx[i] = buf;
+      sx.push_back(buf);
     }
-    e = launch_batch_t<AR_DF64>((const KPlan*)b->batch_dev, mem, sx.data(), ys, nvec, s);
   }
+  if (mem.empty()) return HM_OK;
+  cudaError_t e = dt == HM_F32 ? launch_batch_t<AR_F32>(mem, sx.data(), sy.data(), nvec, s)
+                               : launch_batch_t<AR_DF64>(mem, sx.data(), sy.data(), nvec, s);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return HM_OK;
 }

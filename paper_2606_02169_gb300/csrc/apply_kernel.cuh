@@ -23,6 +23,8 @@
 namespace hm {
 
 constexpr int kNT = 256;  // threads per CTA of the apply kernels
+// bytes of x the CTAs may hold in whole-block work at once (L2 is 129 MB)
+constexpr long long kInflightMax = 48LL << 20;
 
 template <int AR>
 struct Lists {  // per-block uniform values (shared memory)
@@ -403,8 +405,11 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
   const int nchunks = cp.count();
   const long long nitems = P.nblk * nchunks;
   long long cur = -1;
-  // blocks outer when there are enough of them, else (block, chunk) items
-  if (P.nblk >= 2LL * gridDim.x) {
+  // whole blocks per CTA when there are enough of them and the blocks in
+  // flight fit in L2 with room to spare; else (block, chunk) items, so that
+  // the CTAs share a few blocks at a time
+  const long long inflight = (long long)P.B * nvec * sizeof(typename Ar<AR>::TX) * gridDim.x;
+  if (P.nblk >= 2LL * gridDim.x && inflight <= kInflightMax) {
     for (long long blk = blockIdx.x; blk < P.nblk; blk += gridDim.x) {
       eval_block<AR>(P, L, blk, nvec);
       for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, c);
@@ -425,44 +430,61 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
 
 // ---------------------------------------------------------------------------
 // Batched apply: many plans of uneven size in one persistent launch. Work
-// items (instance, low block) are numbered by a prefix sum over instances;
-// CTAs stride over that single index space, so instances of 6561 and of 4.8M
-// states are cut into the same unit of work.
+// items (instance, block) or (instance, block, chunk) are numbered by a
+// prefix sum over instances; CTAs stride over that single index space. The
+// batch's plans travel inside the kernel parameters (__grid_constant__, at
+// most 32 KB), so, like k_apply's single plan, they are read from the
+// constant bank; larger batches take several launches.
 // ---------------------------------------------------------------------------
-constexpr int kBatchMax = 256;
+constexpr int kBatchMax = 128;
 struct BatchArgs {
-  int n, pad;
-  long long blk_start[kBatchMax + 1];
+  int n, by_block;                 // by_block: items are whole blocks, else (block, chunk)
+  long long start[kBatchMax + 1];  // prefix sum of items over instances
   const void* x[kBatchMax];
   void* y[kBatchMax];
+  KPlan plans[kBatchMax];
 };
+static_assert(sizeof(BatchArgs) + 64 <= 32764, "kernel parameter limit");
 
 template <int AR, int S, bool NV1>
 __global__ void __launch_bounds__(kNT, MinBlocks<AR, 0>::v)
-k_batch(const KPlan* __restrict__ plans, const BatchArgs A, int nvec, NvDiv nvdiv, size_t lists_off) {
+k_batch(const __grid_constant__ BatchArgs A, int nvec, NvDiv nvdiv) {
   extern __shared__ __align__(16) unsigned char sm[];
-  KPlan& P = *reinterpret_cast<KPlan*>(sm);
   using TX = typename Ar<AR>::TX;
   using TY = typename Ar<AR>::TY;
-  const long long total = A.blk_start[A.n];
+  const long long total = A.start[A.n];
   int inst = -1;
+  long long cur = -1;
   Lists<AR> L{};
+  ChunkPlan cp{};
+  int nchunks = 1;
   for (long long w = blockIdx.x; w < total; w += gridDim.x) {
     int ni = inst < 0 ? 0 : inst;
-    while (A.blk_start[ni + 1] <= w) ++ni;
+    while (A.start[ni + 1] <= w) ++ni;
+    const KPlan& P = A.plans[ni];
     if (ni != inst) {
       __syncthreads();
-      if (threadIdx.x == 0) P = plans[ni];
-      __syncthreads();
       inst = ni;
-      L = carve<AR>(sm + lists_off, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
+      cur = -1;
+      L = carve<AR>(sm, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
       load_descriptors<AR>(P, L);
+      cp = chunk_plan(P.B * nvec, S);
+      nchunks = cp.count();
     }
-    const long long blk = w - A.blk_start[inst];
-    eval_block<AR>(P, L, blk, nvec);
-    const ChunkPlan cp = chunk_plan(P.B * nvec, S);
-    for (int c = 0; c < cp.count(); ++c)
-      apply_item<AR, S, NV1>(P, L, (const TX*)A.x[inst], (TY*)A.y[inst], nvec, nvdiv, blk, cp, c);
+    const long long local = w - A.start[inst];
+    const TX* xi = (const TX*)A.x[inst];
+    TY* yi = (TY*)A.y[inst];
+    if (A.by_block) {
+      eval_block<AR>(P, L, local, nvec);
+      for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1>(P, L, xi, yi, nvec, nvdiv, local, cp, c);
+    } else {
+      const long long blk = local / nchunks;
+      if (blk != cur) {
+        cur = blk;
+        eval_block<AR>(P, L, blk, nvec);
+      }
+      apply_item<AR, S, NV1>(P, L, xi, yi, nvec, nvdiv, blk, cp, (int)(local - blk * nchunks));
+    }
     __syncthreads();
   }
 }

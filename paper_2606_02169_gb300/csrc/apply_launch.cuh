@@ -102,15 +102,13 @@ cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nve
 }
 
 template <int AR, int S, bool NV1>
-static cudaError_t batch_nv(const KPlan* dplans, const std::vector<const Plan*>& members,
-                               const void* const* xs, void* const* ys, long long nvec, cudaStream_t st) {
-  size_t lists = 0;
+static cudaError_t batch_nv(const std::vector<const Plan*>& members, const void* const* xs, void* const* ys,
+                            long long nvec, cudaStream_t st) {
+  size_t smem = 0;
   for (const Plan* p : members) {
     const KPlan& k = p->k;
-    lists = std::max(lists, lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag));
+    smem = std::max(smem, lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag));
   }
-  const size_t off = (sizeof(KPlan) + 15) & ~size_t(15);
-  const size_t smem = off + lists;
   static size_t attr_set = 0;
   if (smem > 48 * 1024 && smem > attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_batch<AR, S, NV1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -120,18 +118,29 @@ static cudaError_t batch_nv(const KPlan* dplans, const std::vector<const Plan*>&
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<AR, S, NV1>, kNT, smem);
   const int n = (int)members.size();
+  const long long grid0 = (long long)num_sms() * std::max(1, occ);
   for (int c0 = 0; c0 < n; c0 += kBatchMax) {
     BatchArgs A{};
     A.n = std::min(kBatchMax, n - c0);
-    A.blk_start[0] = 0;
+    // whole blocks per item when there are many and the blocks in flight fit
+    // in L2 with room to spare (as in k_apply), else (block, chunk) items
+    long long blocks = 0, bmax = 0;
     for (int i = 0; i < A.n; ++i) {
-      A.blk_start[i + 1] = A.blk_start[i] + members[c0 + i]->nblk;
+      blocks += members[c0 + i]->nblk;
+      bmax = std::max<long long>(bmax, members[c0 + i]->B);
+    }
+    A.by_block = blocks >= 2 * grid0 && bmax * nvec * (long long)sizeof(typename Ar<AR>::TX) * grid0 <= kInflightMax;
+    A.start[0] = 0;
+    for (int i = 0; i < A.n; ++i) {
+      const Plan* m = members[c0 + i];
+      const long long items = A.by_block ? m->nblk : m->nblk * chunk_plan((int)(m->B * nvec), S).count();
+      A.start[i + 1] = A.start[i] + items;
       A.x[i] = xs[c0 + i];
       A.y[i] = ys[c0 + i];
+      A.plans[i] = m->k;
     }
-    long long grid = (long long)num_sms() * std::max(1, occ);
-    grid = std::max<long long>(1, std::min(grid, A.blk_start[A.n]));
-    k_batch<AR, S, NV1><<<(unsigned)grid, kNT, smem, st>>>(dplans + c0, A, (int)nvec, make_nvdiv(nvec), off);
+    const long long grid = std::max<long long>(1, std::min(grid0, A.start[A.n]));
+    k_batch<AR, S, NV1><<<(unsigned)grid, kNT, smem, st>>>(A, (int)nvec, make_nvdiv(nvec));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -139,26 +148,26 @@ static cudaError_t batch_nv(const KPlan* dplans, const std::vector<const Plan*>&
 }
 
 template <int AR, int S>
-static cudaError_t batch_shape(const KPlan* dplans, const std::vector<const Plan*>& members,
-                               const void* const* xs, void* const* ys, long long nvec, cudaStream_t st) {
-  if (nvec == 1) return batch_nv<AR, S, true>(dplans, members, xs, ys, nvec, st);
-  return batch_nv<AR, S, false>(dplans, members, xs, ys, nvec, st);
+static cudaError_t batch_shape(const std::vector<const Plan*>& members, const void* const* xs, void* const* ys,
+                               long long nvec, cudaStream_t st) {
+  if (nvec == 1) return batch_nv<AR, S, true>(members, xs, ys, nvec, st);
+  return batch_nv<AR, S, false>(members, xs, ys, nvec, st);
 }
 
 // One elements-per-thread count for the whole batch, chosen on the median block size.
 template <int AR>
-cudaError_t launch_batch_t(const KPlan* dplans, const std::vector<const Plan*>& members, const void* const* xs,
-                           void* const* ys, long long nvec, cudaStream_t st) {
+cudaError_t launch_batch_t(const std::vector<const Plan*>& members, const void* const* xs, void* const* ys,
+                           long long nvec, cudaStream_t st) {
   std::vector<long long> be;
   for (const Plan* p : members) be.push_back((long long)p->B * nvec);
   std::nth_element(be.begin(), be.begin() + be.size() / 2, be.end());
   const Shape sh = pick_shape(be[be.size() / 2]);
   switch (sh.s) {
-    case 8: return batch_shape<AR, 8>(dplans, members, xs, ys, nvec, st);
-    case 6: return batch_shape<AR, 6>(dplans, members, xs, ys, nvec, st);
-    case 4: return batch_shape<AR, 4>(dplans, members, xs, ys, nvec, st);
-    case 3: return batch_shape<AR, 3>(dplans, members, xs, ys, nvec, st);
-    default: return batch_shape<AR, 2>(dplans, members, xs, ys, nvec, st);
+    case 8: return batch_shape<AR, 8>(members, xs, ys, nvec, st);
+    case 6: return batch_shape<AR, 6>(members, xs, ys, nvec, st);
+    case 4: return batch_shape<AR, 4>(members, xs, ys, nvec, st);
+    case 3: return batch_shape<AR, 3>(members, xs, ys, nvec, st);
+    default: return batch_shape<AR, 2>(members, xs, ys, nvec, st);
   }
 }
 

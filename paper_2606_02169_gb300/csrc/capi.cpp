@@ -222,7 +222,6 @@ int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out) {
   }
   int rc = batch_setup(b);
   if (rc) {
-    if (b->batch_dev) cudaFree(b->batch_dev);
     delete b;
     return rc;
   }
@@ -256,7 +255,6 @@ int hm_destroy(hm_handle h) {
   free_tiles(p);
   if (p->scratch) cudaFree(p->scratch);
   if (p->xsplit) cudaFree(p->xsplit);
-  if (p->batch_dev) cudaFree(p->batch_dev);
   p->magic = 0;
   delete p;
   return HM_OK;

@@ -237,8 +237,6 @@ struct Plan {
   // batch handle
   bool is_batch = false;
   std::vector<Plan*> members;
-  std::vector<unsigned long long> member_gen;
-  void* batch_dev = nullptr;
   unsigned long long gen = 0;   // bumped by every (re)build of the tables
 };
 

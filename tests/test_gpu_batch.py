@@ -51,3 +51,27 @@ def test_batch_graph_capture():
     torch.cuda.synchronize()
     for h, x, y in zip(hams, xs, ys):
         assert torch.equal(h.apply(x), y)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_mixing_large_and_small_instances(dtype):
+    """Instances that fill the GPU alone take plain launches, the rest the
+    persistent work queue; results equal per-instance hm_apply either way."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Batch
+    from gpu_util import TOL_F64, row_scale_bound
+    models = [W.xxz_spin1_chain(13, seed=61)] + W.disorder_ensemble(count=5, nmin=3, nmax=7, base_seed=62) + \
+        [W.xxz_spin1_chain(12, seed=63)]
+    hams = [ham(m) for m in models]
+    nvec = 2
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    xs = [torch.from_numpy(W.vector(h.D, 200 + i, nvec=nvec)).to("cuda", tdt) for i, h in enumerate(hams)]
+    ys = Batch(hams).apply(xs)
+    torch.cuda.synchronize()
+    for i, h in enumerate(hams):
+        assert torch.equal(h.apply(xs[i]), ys[i]), i
+    # the large instance against the oracle, every row
+    xn = xs[0].double().cpu().numpy()
+    ref = oracle.apply(models[0].sites, models[0].terms, xn, nvec=nvec)
+    scale = np.full(xn.size, row_scale_bound(models[0], np.abs(xn).max()))
+    check_close(ys[0].double().cpu().numpy(), ref, scale, TOL_F32 if dtype == "f32" else TOL_F64, "large")
