@@ -63,17 +63,40 @@ __global__ void k_finish(const double* __restrict__ partial, int n, double* __re
   if (threadIdx.x == 0) out[0] = sqrt_it ? sqrt(s) : s;
 }
 
-// w -= a[0] * v + (bprev ? bprev[0] : 0) * vp
+// w -= a[0] * v + (bprev ? bprev[0] : 0) * vp, fused with the block partials
+// of dot products of the updated w: nd = 1: <w, w>; nd = 2: <v, w> and
+// <vp, w> (partial[b] and partial[gridDim.x + b]). Same grid and thread
+// mapping as k_dot, so the sums keep a fixed order.
 template <class T>
-__global__ void k_axpy2(T* __restrict__ w, const T* __restrict__ v, const T* __restrict__ vp,
-                        const double* __restrict__ a, const double* __restrict__ bprev, long long n) {
+__global__ void __launch_bounds__(kRedThreads) k_axpy2_dot(T* __restrict__ w, const T* __restrict__ v,
+                                                            const T* __restrict__ vp, const double* __restrict__ a,
+                                                            const double* __restrict__ bprev, long long n, int nd,
+                                                            double* __restrict__ partial) {
+  __shared__ double sh[32];
   const double al = a[0];
   const double be = bprev ? bprev[0] : 0.0;
+  double s0 = 0.0, s1 = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double r = tod(w[i]) - al * tod(v[i]);
-    if (vp) r -= be * tod(vp[i]);
-    w[i] = (T)r;
+    const double vi = tod(v[i]);
+    const double pi = vp ? tod(vp[i]) : 0.0;
+    double r = tod(w[i]) - al * vi;
+    if (vp) r -= be * pi;
+    const T wt = (T)r;
+    w[i] = wt;
+    const double wn = tod(wt);  // the stored value, as a later k_dot would read it
+    if (nd == 1) {
+      s0 = fma(wn, wn, s0);
+    } else {
+      s0 = fma(vi, wn, s0);
+      s1 = fma(pi, wn, s1);
+    }
+  }
+  s0 = block_sum(s0, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s0;
+  if (nd == 2) {
+    s1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = s1;
   }
 }
 
@@ -201,10 +224,10 @@ static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, do
   const int vb = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
   const int rb = (int)std::min<long long>((n + kRedThreads - 1) / kRedThreads, kRedBlocks);
   T *V = nullptr;
-  double* dsc = nullptr;  // [rb partials][alpha steps][beta steps][tmp 4]
+  double* dsc = nullptr;  // [2 rb partials][alpha steps][beta steps][tmp 4]
   cudaError_t e = cudaMalloc(&V, sizeof(T) * n * 3);
   if (e != cudaSuccess) return cuda_fail(e, "Lanczos work vectors");
-  e = cudaMalloc(&dsc, sizeof(double) * (rb + 2 * (size_t)steps + 8));
+  e = cudaMalloc(&dsc, sizeof(double) * (2 * (size_t)rb + 2 * (size_t)steps + 8));
   if (e != cudaSuccess) {
     cudaFree(V);
     return cuda_fail(e, "Lanczos scalars");
@@ -213,7 +236,7 @@ static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, do
   T* vp = V + n;
   T* w = V + 2 * n;
   double* part = dsc;
-  double* dal = dsc + rb;
+  double* dal = dsc + 2 * rb;
   double* dbe = dal + steps;
   double* tmp = dbe + steps;
   int rc = HM_OK;
@@ -232,14 +255,21 @@ static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, do
       int arc = apply_on(p, false, vk, w, 1, dt, s, tuned_cfg(p, dt, 1), false);
       if (arc) return arc;
       dot(vk, w, dal + k, 0);
-      k_axpy2<T><<<vb, 256, 0, s>>>(w, vk, k > 0 ? vp : nullptr, dal + k, k > 0 ? dbe + k - 1 : nullptr, n);
-      if (flags & 1) {  // local reorthogonalisation (second Gram-Schmidt pass)
-        dot(vk, w, tmp + 1, 0);
-        if (k > 0) dot(vp, w, tmp + 2, 0);
-        k_axpy2<T><<<vb, 256, 0, s>>>(w, vk, k > 0 ? vp : nullptr, tmp + 1, k > 0 ? tmp + 2 : nullptr, n);
+      const T* vpk = k > 0 ? vp : nullptr;
+      const bool last = k == m - 1;
+      if (flags & 1) {
+        // w -= alpha v_k + beta v_{k-1}, with <v_k, w> and <v_{k-1}, w> of the
+        // result for the second Gram-Schmidt pass
+        k_axpy2_dot<T><<<rb, kRedThreads, 0, s>>>(w, vk, vpk, dal + k, k > 0 ? dbe + k - 1 : nullptr, n, 2, part);
+        k_finish<<<1, 256, 0, s>>>(part, rb, tmp + 1, 0);
+        k_finish<<<1, 256, 0, s>>>(part + rb, rb, tmp + 2, 0);
+        // second pass, fused with beta_k = ||w||
+        k_axpy2_dot<T><<<rb, kRedThreads, 0, s>>>(w, vk, vpk, tmp + 1, k > 0 ? tmp + 2 : nullptr, n, 1, part);
+      } else {
+        k_axpy2_dot<T><<<rb, kRedThreads, 0, s>>>(w, vk, vpk, dal + k, k > 0 ? dbe + k - 1 : nullptr, n, 1, part);
       }
-      if (k == m - 1) break;
-      dot(w, w, dbe + k, 1);
+      if (last) break;
+      k_finish<<<1, 256, 0, s>>>(part, rb, dbe + k, 1);
       std::swap(vp, vk);                         // v_{k-1} <- v_k
       k_scale<T><<<vb, 256, 0, s>>>(vk, w, dbe + k, 0.0, n);  // v_{k+1} = w / beta_k
     }
