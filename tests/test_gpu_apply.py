@@ -148,13 +148,20 @@ def boundary_rows(dims, rng, count):
 
 
 def sampled_parity(model, dtype, seed, n_random, tol):
+    """Full-size apply in the launch configuration the benchmark times (the
+    autotuned one), checked on sampled rows; the library-default launch of
+    the same kernel must give the same y bit for bit."""
     torch = torch_cuda()
     h = ham(model)
     D = h.D
     tdt = torch.float64 if dtype == np.float64 else torch.float32
+    cfg = h.tune(1, tdt)
     x = W.torch_vector(D, seed, dtype=tdt)
     y = h.apply(x)
+    y0 = h.apply_ex(x, kernel="general" if cfg["kernel"] == 1 else "tile")
     torch.cuda.synchronize()
+    assert torch.equal(y, y0), f"tuned launch {cfg} differs from the default launch of its kernel"
+    del y0
     rng = np.random.default_rng(seed)
     rows = np.unique(np.concatenate([rng.integers(0, D, size=n_random),
                                      boundary_rows(model.dims, rng, 2000)]))
