@@ -2,8 +2,8 @@
 //   w = H v_k;  alpha_k = <v_k, w>;  w -= alpha_k v_k + beta_{k-1} v_{k-1};
 //   [optional second Gram-Schmidt pass against v_k, v_{k-1}];
 //   beta_k = ||w||;  v_{k+1} = w / beta_k.
-// Dot products and norms accumulate in FP64 (even for FP32 storage) and are
-// reduced in a fixed order (per-block partials, then one block), so a rerun
+// Dot products and norms accumulate to FP64 accuracy (even for FP32 storage)
+// and are reduced in a fixed order (per-block partials, then one block), so a rerun
 // from the same v0 reproduces every Krylov vector bit for bit. The ground
 // state Ritz vector is assembled in that rerun, so the Krylov basis is never
 // stored. Scalars live on the device between kernels: the step loop has no
@@ -22,12 +22,54 @@ namespace hm {
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
+// Arithmetic of the vector kernels. GB300 executes FP64 FMA at about 1/70 of
+// the FP32 rate, which would make these memory-bound kernels FP64-bound, so
+//   * dot products accumulate a double-float sum of exact (FP32 data) or
+//     Dekker (FP64 data, split as read) products on the FP32 pipe, reduced in
+//     a fixed order (lanes, warps, blocks), then rounded once to FP64;
+//   * updates of FP32 vectors run in double-float and round once to FP32;
+//   * updates of FP64 vectors stay native FP64.
 template <class T>
 __device__ __forceinline__ double tod(T v);
 template <>
 __device__ __forceinline__ double tod<float>(float v) { return f2d_exact(v); }
 template <>
 __device__ __forceinline__ double tod<double>(double v) { return v; }
+
+__device__ __forceinline__ float2 pair_of(float v) { return make_float2(v, 0.0f); }
+__device__ __forceinline__ float2 pair_of(double v) { return split_f64(v); }
+
+// acc += a * b
+__device__ __forceinline__ void dot_acc(DF& acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  df_add(acc, make_float2(p, __fmaf_rn(a, b, -p)));   // exact product
+}
+__device__ __forceinline__ void dot_acc(DF& acc, double a, double b) {
+  const float2 x = split_f64(a), y = split_f64(b);
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  df_add(acc, make_float2(p, e));
+}
+
+// Fixed-order CTA sum of a double-float value; the FP64 result is valid in
+// thread 0.
+__device__ __forceinline__ double block_sum(DF v, float2* sh) {
+  for (int o = 16; o > 0; o >>= 1)
+    df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = make_float2(v.s, v.c);
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    DF t{0.f, 0.f};
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) df_add(t, sh[i]);
+    s = df_to_double(t);
+  }
+  __syncthreads();
+  return s;
+}
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -41,17 +83,25 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
+// x0 + c1 * x1 + c2 * x2 rounded to T (c as double-float pairs, x1, x2 FP32)
+__device__ __forceinline__ float lin3(float x0, float2 c1, float x1, float2 c2, float x2) {
+  DF r{x0, 0.0f};
+  df_fma(r, c1, x1, 0.0f);
+  df_fma(r, c2, x2, 0.0f);
+  return __fadd_rn(r.s, r.c);
+}
+
 // partial[b] = sum over the block's grid-stride share of a[i]*b[i]
 template <class T>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ a, const T* __restrict__ b,
                                                      long long n, double* __restrict__ partial) {
-  __shared__ double sh[32];
-  double s = 0.0;
+  __shared__ float2 sh[32];
+  DF s{0.f, 0.f};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    s = fma(tod(a[i]), tod(b[i]), s);
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    dot_acc(s, a[i], b[i]);
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 // out[0] = sum partial (fixed order); if sqrt_it, out = sqrt(out)
@@ -72,31 +122,49 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy2_dot(T* __restrict__ w, co
                                                             const T* __restrict__ vp, const double* __restrict__ a,
                                                             const double* __restrict__ bprev, long long n, int nd,
                                                             double* __restrict__ partial) {
-  __shared__ double sh[32];
+  __shared__ float2 sh[32];
   const double al = a[0];
   const double be = bprev ? bprev[0] : 0.0;
-  double s0 = 0.0, s1 = 0.0;
+  const float2 mal = pair_of(-al), mbe = pair_of(-be);
+  DF s0{0.f, 0.f}, s1{0.f, 0.f};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double vi = tod(v[i]);
-    const double pi = vp ? tod(vp[i]) : 0.0;
-    double r = tod(w[i]) - al * vi;
-    if (vp) r -= be * pi;
-    const T wt = (T)r;
-    w[i] = wt;
-    const double wn = tod(wt);  // the stored value, as a later k_dot would read it
-    if (nd == 1) {
-      s0 = fma(wn, wn, s0);
+    const T vi = v[i];
+    const T pi = vp ? vp[i] : T(0);
+    T wt;
+    if constexpr (sizeof(T) == 4) {
+      wt = lin3(w[i], mal, vi, mbe, pi);
     } else {
-      s0 = fma(vi, wn, s0);
-      s1 = fma(pi, wn, s1);
+      double r = fma(-al, vi, w[i]);
+      if (vp) r = fma(-be, pi, r);
+      wt = r;
+    }
+    w[i] = wt;
+    if (nd == 1) {
+      dot_acc(s0, wt, wt);
+    } else {
+      dot_acc(s0, vi, wt);
+      dot_acc(s1, pi, wt);
     }
   }
-  s0 = block_sum(s0, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s0;
+  const double t0 = block_sum(s0, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t0;
   if (nd == 2) {
-    s1 = block_sum(s1, sh);
-    if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = s1;
+    const double t1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = t1;
+  }
+}
+
+// dst = src * c (c a double-float pair for FP32 data)
+template <class T>
+__device__ __forceinline__ T scale_one(T x, double c, float2 cp) {
+  if constexpr (sizeof(T) == 4) {
+    const float p = __fmul_rn(cp.x, x);
+    float e = __fmaf_rn(cp.x, x, -p);
+    e = __fmaf_rn(cp.y, x, e);
+    return __fadd_rn(p, e);
+  } else {
+    return x * c;
   }
 }
 
@@ -106,24 +174,29 @@ __global__ void k_scale(T* __restrict__ v, const T* __restrict__ w, const double
                         double tol, long long n) {
   const double bb = b[0];
   const double inv = (bb > tol) ? 1.0 / bb : 0.0;
+  const float2 ip = pair_of(inv);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    v[i] = (T)(tod(w[i]) * inv);
+    v[i] = scale_one(w[i], inv, ip);
 }
 
 // psi += coef * v
 template <class T>
 __global__ void k_axpy(T* __restrict__ psi, const T* __restrict__ v, double coef, long long n) {
+  const float2 cp = pair_of(coef), zero = make_float2(0.f, 0.f);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    psi[i] = (T)(tod(psi[i]) + coef * tod(v[i]));
+       i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) psi[i] = lin3(psi[i], cp, v[i], zero, 0.0f);
+    else psi[i] = fma(coef, v[i], psi[i]);
+  }
 }
 
 template <class T>
 __global__ void k_copy_scaled(T* __restrict__ dst, const T* __restrict__ src, double scale, long long n) {
+  const float2 sp = pair_of(scale);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    dst[i] = (T)(tod(src[i]) * scale);
+    dst[i] = scale_one(src[i], scale, sp);
 }
 
 // ---------------------------------------------------------------------------
