@@ -67,6 +67,7 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
     long long kk[V];
     uint32_t pk[V];
     float2 g1[V];  // gy of the row (nvec == 1)
+    float2 d0[V];  // sum_v gy x of the row itself: shared by every diagonal channel
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       lo[v] = lo0 + lane + 32 * v;
@@ -75,6 +76,16 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
       kk[v] = hb * P.B + lo[v];
       pk[v] = __ldg(P.ptab + lo[v]);
       g1[v] = (nvec == 1 && ok[v]) ? as_pair(gy[kk[v]]) : make_float2(0.f, 0.f);
+      d0[v] = make_float2(0.f, 0.f);
+      if (ok[v]) {
+        if (nvec == 1) {
+          d0[v] = pair_mul(g1[v], as_pair(x[kk[v]]));
+        } else {
+          DF sd{0.f, 0.f};
+          for (long long u = 0; u < nvec; ++u) df_add(sd, pair_mul(as_pair(gy[kk[v] * nvec + u]), as_pair(x[kk[v] * nvec + u])));
+          d0[v] = df_norm(sd);
+        }
+      }
     }
     int cur = -1;
     DF acc{0.f, 0.f};
@@ -108,7 +119,9 @@ k_term_grad(const KPlan P, const T* __restrict__ gy, const T* __restrict__ x, lo
         const int nj = single ? 0 : (sj.is_low ? low_digit(pk[v], sj.lbit, sj.lwid) : hi_j);
         const float2 cf = P.ttab_df[ch.tab + ni * ch.dj + nj];
         if (ok[v] && cf.x != 0.0f) {
-          if (nvec == 1) {
+          if (ch.off == 0) {
+            df_fma(acc, cf, d0[v].x, d0[v].y);
+          } else if (nvec == 1) {
             const float2 t = pair_mul(g1[v], as_pair(x[kk[v] + ch.off]));
             df_fma(acc, cf, t.x, t.y);
           } else {
