@@ -22,6 +22,7 @@ namespace hm {
 // input element as a (hi, lo) float pair
 __device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f); }
 __device__ __forceinline__ float2 as_pair(double v) { return split_f64(v); }
+__device__ __forceinline__ float2 as_pair(float2 v) { return v; }  // already split
 
 // product of two float pairs without the lo*lo term: (s, c) with s + c equal
 // to a * b to about 2^-46 relative
@@ -162,6 +163,22 @@ int grad_grid(const Plan* p) {
 size_t grad_smem(const Plan* p) { return (size_t)kGradWarps * std::max<size_t>(1, p->terms.size()) * 8; }
 
 // Term gradients into gcoef using `partial` (grid*nterms doubles) as scratch.
+// gy and x already split into float pairs (FP64 data)
+static int launch_term_grad_split(const Plan* p, const float2* gy, const float2* x, double* gcoef, long long nvec,
+                                  double* partial, int grid, cudaStream_t s) {
+  const int nterms = (int)p->terms.size();
+  if (nterms == 0) return HM_OK;
+  const size_t smem = grad_smem(p);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_term_grad<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_term_grad<float2><<<grid, 256, smem, s>>>(p->k, gy, x, nvec, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "term gradient launch");
+  k_reduce_partials<<<(nterms + 255) / 256, 256, 0, s>>>(partial, grid, nterms, gcoef);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
+  return HM_OK;
+}
+
 int launch_term_grad(const Plan* p, const void* gy, const void* x, double* gcoef, long long nvec,
                      hm_dtype dt, double* partial, int grid, cudaStream_t s) {
   const int nterms = (int)p->terms.size();
@@ -210,6 +227,13 @@ int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gco
       return cuda_fail(e, "gradient scratch allocation");
     }
     p->scratch_bytes = need;
+  }
+  if (dt == HM_F64) {  // split gy and x once instead of at every gather
+    const float2 *gs = nullptr, *xs = nullptr;
+    int rc = split_vector(p, 1, gy, p->D * nvec, s, &gs);
+    if (rc == HM_OK) rc = split_vector(p, 0, x, p->D * nvec, s, &xs);
+    if (rc) return rc;
+    return launch_term_grad_split(p, gs, xs, gcoef, nvec, (double*)p->scratch, grid, s);
   }
   return launch_term_grad(p, gy, x, gcoef, nvec, dt, (double*)p->scratch, grid, s);
 }

@@ -48,10 +48,10 @@ __global__ void __launch_bounds__(256) k_split_f64_scalar(const double* __restri
     xs[i] = split_f64(__ldcs(x + i));
 }
 
-// Plan-owned buffer for the split input, grown on demand (stream-ordered:
-// the previous users of the old buffer on `s` finish before it is freed).
-static void* split_buffer(Plan* p, size_t bytes, cudaStream_t s, int* rc) {
-  if (p->xsplit_bytes >= bytes) return p->xsplit;
+// Plan-owned device buffer grown on demand (stream-ordered: the previous
+// users of the old buffer on `s` finish before it is freed).
+static void* grow_buffer(void*& buf, size_t& cap, size_t bytes, cudaStream_t s, int* rc) {
+  if (cap >= bytes) return buf;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   if (cs != cudaStreamCaptureStatusNone) {
@@ -60,17 +60,22 @@ static void* split_buffer(Plan* p, size_t bytes, cudaStream_t s, int* rc) {
     return nullptr;
   }
   cudaError_t e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && p->xsplit) e = cudaFree(p->xsplit);
-  p->xsplit = nullptr;
-  p->xsplit_bytes = 0;
-  if (e == cudaSuccess) e = cudaMalloc(&p->xsplit, bytes);
+  if (e == cudaSuccess && buf) e = cudaFree(buf);
+  buf = nullptr;
+  cap = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&buf, bytes);
   if (e != cudaSuccess) {
-    p->xsplit = nullptr;
+    buf = nullptr;
     *rc = cuda_fail(e, "FP64 split buffer");
     return nullptr;
   }
-  p->xsplit_bytes = bytes;
-  return p->xsplit;
+  cap = bytes;
+  return buf;
+}
+
+// the split input of the apply
+static void* split_buffer(Plan* p, size_t bytes, cudaStream_t s, int* rc) {
+  return grow_buffer(p->xsplit, p->xsplit_bytes, bytes, s, rc);
 }
 
 cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
@@ -80,6 +85,19 @@ cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
   else
     k_split_f64_scalar<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n);
   return cudaGetLastError();
+}
+
+// n FP64 values split into the plan's buffer `which` (0: the apply's, 1: a
+// second one), for kernels that read both gy and x split.
+int split_vector(Plan* p, int which, const void* x, long long n, cudaStream_t s, const float2** out) {
+  int rc = HM_OK;
+  void* buf = which == 0 ? split_buffer(p, (size_t)n * sizeof(float2), s, &rc)
+                         : grow_buffer(p->gsplit, p->gsplit_bytes, (size_t)n * sizeof(float2), s, &rc);
+  if (!buf) return rc;
+  cudaError_t e = split_into(x, buf, n, s);
+  if (e != cudaSuccess) return cuda_fail(e, "FP64 split launch");
+  *out = (const float2*)buf;
+  return HM_OK;
 }
 
 // y = H x (or H^T x) on stream s. Kernel: cfg.kern = 2 the tile kernel (an

@@ -255,6 +255,7 @@ int hm_destroy(hm_handle h) {
   free_tiles(p);
   if (p->scratch) cudaFree(p->scratch);
   if (p->xsplit) cudaFree(p->xsplit);
+  if (p->gsplit) cudaFree(p->gsplit);
   p->magic = 0;
   delete p;
   return HM_OK;

@@ -210,9 +210,12 @@ struct Plan {
   void* dev = nullptr;        // one device allocation holding every table
   size_t dev_bytes = 0;
 
-  // FP64 input split into float pairs, one vector (grown on demand)
+  // FP64 input split into float pairs, one vector (grown on demand); a second
+  // buffer for kernels that read two split vectors (the gradients' gy)
   void* xsplit = nullptr;
   size_t xsplit_bytes = 0;
+  void* gsplit = nullptr;
+  size_t gsplit_bytes = 0;
 
   // scratch for the adjoint reduction (grown on demand)
   void* scratch = nullptr;
@@ -265,6 +268,7 @@ int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, c
 int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64);
 TuneCfg tuned_cfg(Plan* p, hm_dtype dt, long long nvec);
+int split_vector(Plan* p, int which, const void* x, long long n, cudaStream_t s, const float2** out);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
 int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,
