@@ -128,8 +128,11 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
  *                  nterms doubles, overwritten), O_t = op_i op_j without coef.
  * gy, x: device vectors of dtype. gcoef is always FP64, reduced
  * deterministically (fixed-order two-pass reduction, no atomics). Uses
- * library-owned scratch of O(nterms * grid) doubles per plan; calls on the
- * same plan must not overlap on the GPU. */
+ * library-owned scratch of O(nterms * grid) doubles per plan and, for
+ * HM_F64 gradients, two plan-owned buffers of D*nvec float pairs (gy and x
+ * split once); all grow on demand, so the first call of a size should come
+ * before any stream capture. Calls on the same plan must not overlap on the
+ * GPU. */
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
                      int64_t nvec, hm_dtype dtype, void* stream);
 
