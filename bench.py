@@ -541,6 +541,23 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     del xs, ys, b, hams, g
     torch.cuda.empty_cache()
 
+    # the paper's Table I models (Sec. V testbeds C1, C2), FP64, one apply =
+    # one matvec; the paper's matrix-free CPU rates (unstated CPU) as context
+    for name, mk, paper in (("paper_c1_f64", W.paper_c1_chain, 6.137), ("paper_c2_f64", W.paper_c2_chain, 0.04387)):
+        mc = mk()
+        hc = Hamiltonian(mc.sites, mc.terms)
+        if args.tune:
+            hc.tune(1, torch.float64)
+        xc = W.torch_vector(hc.D, 12, dtype=torch.float64)
+        yc = torch.empty_like(xc)
+        k = 20
+        ms = timed(lambda: hc.apply(xc, out=yc), k, 3, 1, stream) / k
+        out[name] = {"D": hc.D, "matvec_per_s": 1e3 / ms, "gstates_s": hc.D / ms / 1e6,
+                     "paper_matrix_free_cpu_matvec_per_s": paper,
+                     "note": "paper figure: Table I, CPU unstated; context only"}
+        del hc, xc, yc
+        torch.cuda.empty_cache()
+
     # adjoint on the 4x5 lattice (D = 2^20, FP64): H^T gy + 113 coupling gradients
     ml = W.square_lattice_xxz(4, 5, seed=4)
     hl = Hamiltonian(ml.sites, ml.terms)

@@ -185,6 +185,13 @@ def test_tavis_cummings_1e9_sampled(dtype, tol):
     sampled_parity(W.tavis_cummings(24, 64, seed=7), dtype, 8, 20000, tol)
 
 
+@pytest.mark.parametrize("dtype,tol", [(np.float64, TOL_F64), (np.float32, TOL_F32)])
+@pytest.mark.parametrize("model", [W.paper_c1_chain(), W.paper_c2_chain()], ids=["c1_spin1_pbc", "c2_mixed_pbc"])
+def test_paper_table1_models_sampled(model, dtype, tol):
+    """The paper's Sec. V testbeds C1 (D = 3^15) and C2 (D = 24^6), periodic."""
+    sampled_parity(model, dtype, 13, 20000, tol)
+
+
 def test_index_past_2_31_sampled():
     """D = 2 * 3^19 > 2^31: 64-bit source offsets and digit decoding."""
     m = W.xxz_spin1_chain(19, seed=77)
