@@ -107,11 +107,14 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
              TuneCfg cfg, bool native_f64) {
   const KPlan& k = transpose ? p->kt : p->k;
   const KTile* tk = cfg.kern == 2 ? get_tile(p, nvec, transpose, s) : nullptr;
-  if (cfg.kern == 2 && !tk) {
-    set_error("this plan has no tile form for that nvec");
+  if (cfg.kern == 2 && !tk && cfg.strict) {
+    set_error("this plan has no tile form for that nvec (or its tables cannot be built during stream capture)");
     return HM_ERR_UNSUPPORTED;
   }
-  const TuneCfg gcfg = cfg;
+  // a tuned tile choice whose tables are unavailable (e.g. first use inside a
+  // stream capture) runs the general kernel with its default shape
+  TuneCfg gcfg = cfg;
+  if (cfg.kern == 2) gcfg = TuneCfg{};
   cudaError_t e;
   const void* xin = x;
   if (dt == HM_F64 && !native_f64) {
@@ -128,7 +131,7 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
     if (dt == HM_F32) e = launch_tile_t<AR_F32>(*tk, xin, y, s, cfg);
     else if (native_f64) e = launch_tile_t<AR_F64>(*tk, xin, y, s, cfg);
     else e = launch_tile_t<AR_DF64>(*tk, xin, y, s, cfg);
-    if (e == cudaErrorInvalidConfiguration && cfg.kern == 2) {
+    if (e == cudaErrorInvalidConfiguration && cfg.strict) {
       set_error("tile kernel needs more shared memory than a CTA has");
       return HM_ERR_UNSUPPORTED;
     }

@@ -157,6 +157,7 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
     return HM_ERR_INVALID_ARG;
   }
   cfg.kern = tile ? 2 : (general ? 1 : 0);
+  cfg.strict = 1;
   if (tile && cfg.s && cfg.s != 1 && cfg.s != 2 && cfg.s != 4) {
     set_error("tile kernel rows per iteration must be 0 (default), 1, 2 or 4");
     return HM_ERR_INVALID_ARG;
@@ -328,6 +329,7 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
       TuneCfg c;
       c.kern = 2;
       c.s = rs;
+      c.strict = 1;  // time the tile kernel itself, never a fallback
       const float t = time_cfg(c);
       if (rc == HM_ERR_UNSUPPORTED) {  // tile kernel cannot launch for this plan
         rc = HM_OK;
@@ -349,6 +351,7 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
   cudaFree(x);
   cudaFree(y);
   if (rc != HM_OK) return rc;
+  best.strict = 0;  // a stored choice may fall back (see apply_on)
   p->tuned[{(int)dtype, (long long)nvec}] = best;
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tune_cache[sig] = best;

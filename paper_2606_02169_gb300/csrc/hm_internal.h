@@ -180,6 +180,7 @@ struct TuneCfg {
   int s = 0;     // elements per thread (rows of a chunk)
   int mb = 0;    // 1: register cap for one more resident CTA per SM
   int kern = 0;  // 0: library choice, 1: general kernel, 2: tile kernel
+  int strict = 0;  // 1: an explicit request (hm_apply_ex) -- no fallback
 };
 
 struct Channel {            // host-side merged channel
