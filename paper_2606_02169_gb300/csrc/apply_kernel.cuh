@@ -410,9 +410,24 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
   // the CTAs share a few blocks at a time
   const long long inflight = (long long)P.B * nvec * sizeof(typename Ar<AR>::TX) * gridDim.x;
   if (P.nblk >= 2LL * gridDim.x && inflight <= kInflightMax) {
-    for (long long blk = blockIdx.x; blk < P.nblk; blk += gridDim.x) {
+    // full rounds of whole blocks; the blocks of a last round that would
+    // leave most CTAs idle are cut into (block, chunk) items so that every
+    // CTA shares that round
+    long long full = (P.nblk / gridDim.x) * gridDim.x;
+    if (2 * (P.nblk - full) >= gridDim.x) full = P.nblk;
+    for (long long blk = blockIdx.x; blk < full; blk += gridDim.x) {
       eval_block<AR>(P, L, blk, nvec);
       for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, c);
+      __syncthreads();
+    }
+    const long long rest = (P.nblk - full) * nchunks;
+    for (long long w = blockIdx.x; w < rest; w += gridDim.x) {
+      const long long blk = full + w / nchunks;
+      if (blk != cur) {
+        cur = blk;
+        eval_block<AR>(P, L, blk, nvec);
+      }
+      apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (blk - full) * nchunks));
       __syncthreads();
     }
   } else {
