@@ -10,7 +10,8 @@ from gpu_util import TOL_F32, TOL_F64, abs_bound, check_close, ham, row_scale_bo
 pytestmark = pytest.mark.gpu
 
 # dims chosen to hit: no high sites; 1-2 high sites; ragged low blocks;
-# a boson as a high site and as the low block; a single site above 4096
+# a boson as a high site and as the low block; single sites of 4500 and of
+# 9000 levels (the latter above the 8192-state low-block bound)
 SMALL = [
     ((2,), None),
     ((3,), None),
@@ -21,7 +22,8 @@ SMALL = [
     ((64, 2, 2, 2, 2, 2, 2, 2), ["boson"] + ["spin"] * 7),       # boson high
     ((2, 2, 2, 2, 2, 2, 2, 64), ["spin"] * 7 + ["boson"]),       # boson in the low block
     ((3, 5, 2, 7, 3, 2, 2, 3), ["spin", "boson", "spin", "boson", "spin", "spin", "spin", "spin"]),
-    ((4500,), ["boson"]),                                        # one site above 4096
+    ((4500,), ["boson"]),                                        # one large site
+    ((9000,), ["boson"]),                                        # one site above the block bound
     ((4, 4500), ["spin", "boson"]),
 ]
 
