@@ -26,7 +26,6 @@ CASES = [
     ((64, 2, 2, 2, 2, 2, 2, 2), ["boson"] + ["spin"] * 7),
     ((2, 2, 2, 2, 2, 2, 2, 64), ["spin"] * 7 + ["boson"]),
     ((3, 5, 2, 7, 3, 2, 2, 3), ["spin", "boson", "spin", "boson", "spin", "spin", "spin", "spin"]),
-    ((9000,), ["boson"]),                      # one site above the 8192-state block bound
 ]
 
 
