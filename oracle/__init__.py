@@ -15,6 +15,11 @@ Contents
     (Sec. I: Krylov solvers need only y = H x).
   * ``term_gradients``    -- <gy| O_t |x> per term, by applying one-term
     Hamiltonians; ``hellmann_feynman`` -- <psi|O_t|psi>.
+  * ``sector_*``          -- the globally constrained sector of Sec. VI case 2
+    (local digits summing to a fixed total; App. D): enumeration of the
+    retained states, combinatorial rank / unrank, the projected apply
+    P H P^T x, and a row-wise restatement of the case-2 steps (unpack target,
+    undo the local move, look the source up, accumulate).
 
 Parity pins live in tests/test_oracle_*.py (closed forms, invariants, brute
 force); every oracle function there is pinned to something other than itself.
@@ -300,3 +305,131 @@ def term_gradients(sites, terms, gy, x, nthreads=0):
         Ox = apply(sites, one, x, nthreads=nthreads)
         g[t] = np.vdot(gy, Ox)
     return g
+
+
+# ---------------------------------------------------------------------------
+# Globally constrained sector (Sec. VI case 2, App. D): the retained states
+# are those whose local digits sum to a fixed total K (for spins the fixed
+# magnetization sum_i m_i = K - sum_i s_i; for the Jaynes-Cummings /
+# Tavis-Cummings models the excitation number). Packed storage index = the
+# state's position among the retained states in ascending full-basis order.
+# ---------------------------------------------------------------------------
+
+def sector_basis(sites, total):
+    """Full-basis indices of the retained states, ascending (by enumeration of
+    every digit tuple; small D only)."""
+    s = np.zeros(1, dtype=np.int64)
+    for _, d in sites:   # site 0 outermost: flat index = sum_k n_k M_k (Sec. III)
+        s = (s[:, None] + np.arange(int(d), dtype=np.int64)[None, :]).reshape(-1)
+    return np.nonzero(s == int(total))[0]
+
+
+def sector_counts(dims, total):
+    """cnt[k][r] = number of digit tuples of sites k..N-1 whose sum is r."""
+    N = len(dims)
+    cnt = [[0] * (total + 1) for _ in range(N + 1)]
+    cnt[N][0] = 1
+    for k in range(N - 1, -1, -1):
+        for r in range(total + 1):
+            cnt[k][r] = sum(cnt[k + 1][r - m] for m in range(min(int(dims[k]) - 1, r) + 1))
+    return cnt
+
+
+def sector_dimension(sites, total):
+    dims = [int(d) for _, d in sites]
+    return sector_counts(dims, total)[0][total] if total >= 0 else 0
+
+
+def sector_rank(dims, total, digits, cnt=None):
+    """Packed index of a digit tuple: the number of retained tuples that
+    precede it in lexicographic (= full-index) order, counted site by site
+    (combinatorial ranking); -1 if the tuple is not in the sector."""
+    cnt = cnt or sector_counts(dims, total)
+    rank, rem = 0, total
+    for k, n in enumerate(digits):
+        n = int(n)
+        if n < 0 or n >= dims[k]:
+            return -1
+        for m in range(n):
+            if rem - m >= 0:
+                rank += cnt[k + 1][rem - m]
+        rem -= n
+        if rem < 0:
+            return -1
+    return rank if rem == 0 else -1
+
+
+def sector_unrank(dims, total, r, cnt=None):
+    """Digit tuple of packed index r (inverse of sector_rank)."""
+    cnt = cnt or sector_counts(dims, total)
+    digits, rem = [], total
+    for k in range(len(dims)):
+        m = 0
+        while True:
+            c = cnt[k + 1][rem - m] if rem - m >= 0 else 0
+            if r < c:
+                break
+            r -= c
+            m += 1
+        digits.append(m)
+        rem -= m
+    return digits
+
+
+def sector_apply(sites, terms, total, x, nvec=1, coefs=None):
+    """y = P H P^T x on the packed sector vector (P selects the retained rows
+    of the full basis): the full-basis oracle applied to x embedded with zeros
+    outside the sector, restricted back to the sector. Equal to the action of
+    H inside the sector when H conserves the digit sum."""
+    basis = sector_basis(sites, total)
+    D = dimension(sites)
+    x = np.asarray(x).reshape(basis.size, nvec)
+    xf = np.zeros((D, nvec), dtype=np.result_type(x.dtype, np.float64))
+    xf[basis] = x
+    y = apply(sites, terms, xf.reshape(-1), coefs=coefs, nvec=nvec).reshape(D, nvec)
+    return y[basis].reshape(-1)
+
+
+def sector_rows(sites, terms, total, x, rows, nvec=1):
+    """y_F for packed target rows F, following the case-2 steps of Sec. VI /
+    App. D one by one: unpack the target's digits, undo each term's local move
+    (every source digit pair with a nonzero local matrix element), look the
+    source up in the sector (a failed lookup contributes nothing), accumulate
+    coefficient x x[source]. Row by row in Python: a few thousand rows."""
+    dims = [int(d) for _, d in sites]
+    cnt = sector_counts(dims, total)
+    mats = {}
+
+    def mat(site, op):
+        key = (site, op)
+        if key not in mats:
+            kind, d = sites[site]
+            mats[key] = local_matrix(kind, d, op)
+        return mats[key]
+    x = np.asarray(x).reshape(-1, nvec)
+    out = np.zeros((len(rows), nvec), dtype=np.complex128)
+    for o, F in enumerate(rows):
+        tgt = sector_unrank(dims, total, int(F), cnt)
+        for (i, oi, j, oj, c) in terms:
+            A = mat(i, oi)
+            if j < 0 or oj in ("I", 0):
+                B, j = None, -1
+            else:
+                B = mat(j, oj)
+            for si in range(dims[i]):
+                a = A[tgt[i], si]
+                if a == 0:
+                    continue
+                js = [None] if B is None else range(dims[j])
+                for sj in js:
+                    b = 1.0 if sj is None else B[tgt[j], sj]
+                    if b == 0:
+                        continue
+                    src = list(tgt)
+                    src[i] = si
+                    if sj is not None:
+                        src[j] = sj
+                    I = sector_rank(dims, total, src, cnt)
+                    if I >= 0:
+                        out[o] += c * a * b * x[I]
+    return out.reshape(-1)
