@@ -91,6 +91,22 @@ enum {
 int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
               hm_handle* out);
 
+/* Plan restricted to a globally constrained sector (Sec. VI case 2, App. D):
+ * the retained basis is every digit tuple with sum_k n_k = digit_total (for
+ * spins the fixed magnetization M = digit_total - sum_k s_k; for spin-boson
+ * models the excitation number), packed in ascending full-basis order, and
+ * vectors hold those hm_dim(h) retained states (state-major, nvec values
+ * each). A source's packed index is found by combinatorial ranking, updated
+ * per hop from the target's (no search). Every term must conserve the digit
+ * sum (else HM_ERR_UNSUPPORTED); digit_total outside [0, sum_k (d_k - 1)]
+ * gives HM_ERR_INVALID_ARG, above 255 HM_ERR_UNSUPPORTED. hm_apply,
+ * hm_set_coefficients, hm_lanczos, hm_dim, hm_num_terms and hm_destroy
+ * accept sector plans (apply arithmetic: FP64 accumulation for both dtypes);
+ * hm_apply_ex, hm_apply_adjoint, hm_coupling_gradients_static, hm_tune and
+ * batches return HM_ERR_UNSUPPORTED. */
+int hm_create_sector(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
+                     int64_t digit_total, hm_handle* out);
+
 /* Replace all term coefficients (host array of nterms doubles) without
  * re-planning (Sec. VII: repeatedly rebuilt Hamiltonians). Synchronous. The
  * new list must not make any matrix element imaginary; channels whose

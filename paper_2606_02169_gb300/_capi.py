@@ -32,7 +32,7 @@ HM_LANCZOS_BREAKDOWN = 1
 # Every exported entry point and its signature; tests check that the library
 # exports exactly these names.
 EXPORTS = [
-    "hm_create", "hm_set_coefficients", "hm_dim", "hm_num_terms", "hm_apply", "hm_apply_ex",
+    "hm_create", "hm_create_sector", "hm_set_coefficients", "hm_dim", "hm_num_terms", "hm_apply", "hm_apply_ex",
     "hm_apply_adjoint", "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune",
     "hm_tuned_config", "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export", "hm_coupling_gradients_static",
 ]
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     H = ctypes.c_void_p
     lib.hm_create.argtypes = [ctypes.POINTER(hm_site), i32, ctypes.POINTER(hm_term), i32,
                               ctypes.POINTER(H)]
+    lib.hm_create_sector.argtypes = [ctypes.POINTER(hm_site), i32, ctypes.POINTER(hm_term), i32, i64,
+                                     ctypes.POINTER(H)]
     lib.hm_set_coefficients.argtypes = [H, dp]
     lib.hm_dim.argtypes = [H]
     lib.hm_dim.restype = i64
@@ -95,7 +97,7 @@ def load(path: str = LIB_PATH):
     lib.hm_strerror.argtypes = [ctypes.c_int]
     lib.hm_strerror.restype = ctypes.c_char_p
     lib.hm_last_error.restype = ctypes.c_char_p
-    for name in ("hm_create", "hm_set_coefficients", "hm_apply", "hm_apply_ex", "hm_apply_adjoint",
+    for name in ("hm_create", "hm_create_sector", "hm_set_coefficients", "hm_apply", "hm_apply_ex", "hm_apply_adjoint",
                  "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune", "hm_tuned_config",
                  "hm_destroy"):
         getattr(lib, name).restype = ctypes.c_int

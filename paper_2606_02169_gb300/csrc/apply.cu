@@ -105,6 +105,7 @@ int split_vector(Plan* p, int which, const void* x, long long n, cudaStream_t s,
 // general kernel's instructions per state), otherwise the general kernel.
 int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64) {
+  if (p->sector) return launch_sector(p, x, y, nvec, dt, s);  // the Lanczos driver on a sector plan
   const KPlan& k = transpose ? p->kt : p->k;
   const KTile* tk = cfg.kern == 2 ? get_tile(p, nvec, transpose, s) : nullptr;
   if (cfg.kern == 2 && !tk && cfg.strict) {

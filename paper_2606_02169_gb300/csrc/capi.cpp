@@ -45,8 +45,8 @@ int check_vec_args(const Plan* p, const void* x, const void* y, long long nvec, 
     set_error("vector pointers must be aligned to the element size");
     return HM_ERR_INVALID_ARG;
   }
-  if ((double)p->D * (double)nvec > 9.0e18) { set_error("D * nvec overflows int64"); return HM_ERR_OVERFLOW; }
-  if (overlap(x, y, (size_t)(p->D * nvec) * esize(dt))) {
+  if ((double)vec_states(p) * (double)nvec > 9.0e18) { set_error("D * nvec overflows int64"); return HM_ERR_OVERFLOW; }
+  if (overlap(x, y, (size_t)(vec_states(p) * nvec) * esize(dt))) {
     set_error("x and y overlap (the pull form needs x read-only while y is written)");
     return HM_ERR_ALIAS;
   }
@@ -105,6 +105,42 @@ int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_
   return HM_OK;
 }
 
+int hm_create_sector(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
+                     int64_t digit_total, hm_handle* out) {
+  if (!out) { set_error("out is NULL"); return HM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!sites || nsites < 1 || nterms < 0 || (nterms > 0 && !terms)) {
+    set_error("sites/terms arrays invalid");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (nsites > kMaxSites) { set_error("nsites must be in [1, 64]"); return HM_ERR_INVALID_ARG; }
+  Plan* p = new Plan();
+  p->N = nsites;
+  p->sites.assign(sites, sites + nsites);
+  p->terms.assign(terms, terms + nterms);
+  p->sector = true;
+  p->sec_total = digit_total;
+  cudaGetDevice(&p->device);
+  int rc = plan_check(p);
+  if (rc == HM_OK) rc = build_plan(p);   // builds the sector tables too
+  if (rc != HM_OK) {
+    free_plan_device(p);
+    free_sector(p);
+    delete p;
+    return rc;
+  }
+  *out = reinterpret_cast<hm_handle>(p);
+  return HM_OK;
+}
+
+static int no_sector(const Plan* p, const char* what) {
+  if (p && p->sector) {
+    set_error(std::string(what) + " is not available for sector plans (hm_create_sector)");
+    return HM_ERR_UNSUPPORTED;
+  }
+  return HM_OK;
+}
+
 int hm_set_coefficients(hm_handle h, const double* coefs) {
   Plan* p = as_plan(h);
   if (!p || p->is_batch || !coefs) { set_error("invalid handle or coefficients"); return HM_ERR_INVALID_ARG; }
@@ -126,7 +162,7 @@ int hm_set_coefficients(hm_handle h, const double* coefs) {
 int64_t hm_dim(hm_handle h) {
   Plan* p = as_plan(h);
   if (!p) return HM_ERR_INVALID_ARG;
-  return p->D;
+  return vec_states(p);
 }
 
 int32_t hm_num_terms(hm_handle h) {
@@ -139,6 +175,7 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
   Plan* p = as_plan(h);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
+  if (p->sector) return launch_sector(p, x, y, nvec, dtype, (cudaStream_t)stream);
   return launch_apply(p, x, y, nvec, dtype, (cudaStream_t)stream, tuned_cfg(p, dtype, nvec));
 }
 
@@ -147,6 +184,7 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
   Plan* p = as_plan(h);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
+  if ((rc = no_sector(p, "hm_apply_ex"))) return rc;
   TuneCfg cfg;
   cfg.ctas = ctas > 0 ? ctas : 0;
   cfg.mb = (flags >> 2) & 1;
@@ -174,6 +212,7 @@ int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, doubl
                      int64_t nvec, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
   if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
+  if (int rc = no_sector(p, "hm_apply_adjoint")) return rc;
   if (!gx && !gcoef) return HM_OK;
   if (gx) {
     int rc = check_vec_args(p, gy, gx, nvec, dtype);
@@ -214,9 +253,9 @@ int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out) {
   b->is_batch = true;
   for (int i = 0; i < n; ++i) {
     Plan* p = as_plan(hs[i]);
-    if (!p || p->is_batch) {
+    if (!p || p->is_batch || p->sector) {
       delete b;
-      set_error("batch member " + std::to_string(i) + " is not a plan handle");
+      set_error("batch member " + std::to_string(i) + " is not a full-basis plan handle");
       return HM_ERR_INVALID_ARG;
     }
     b->members.push_back(p);
@@ -254,6 +293,7 @@ int hm_destroy(hm_handle h) {
   cudaDeviceSynchronize();
   free_plan_device(p);
   free_tiles(p);
+  free_sector(p);
   if (p->scratch) cudaFree(p->scratch);
   if (p->xsplit) cudaFree(p->xsplit);
   if (p->gsplit) cudaFree(p->gsplit);
@@ -276,6 +316,7 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
     set_error("invalid tune arguments");
     return HM_ERR_INVALID_ARG;
   }
+  if (int rc = no_sector(p, "hm_tune")) return rc;
   const std::string sig = tune_signature(p, dtype, nvec);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);

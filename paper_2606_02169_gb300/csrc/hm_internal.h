@@ -174,6 +174,39 @@ struct KTile {
   const double* fs_d; const float2* fs_df; const float* fs_f;  // [fs_w * F]
 };
 
+// ---------------------------------------------------------------------------
+// Fixed digit-sum sector (Sec. VI case 2, App. D): retained states are the
+// digit tuples with sum_k n_k = K, packed in ascending full-index order. The
+// packed index of a tuple is its combinatorial rank
+//   rank(n) = sum_k A_k[K - P_k][n_k],   P_k = n_0 + ... + n_{k-1},
+//   A_k[t][n] = sum_{m<n} cnt_{k+1}[t - m],
+// with cnt_k[t] the number of digit tuples of sites k..N-1 summing to t.
+// A hop that changes sites i < j by -q_i, -q_j (q_i + q_j = 0) changes only
+// the terms of sites i..j, so the source rank is the target's plus O(j-i+1)
+// table differences: the lookup of Sec. VI without a search.
+// ---------------------------------------------------------------------------
+struct KSecChan {
+  int tab;         // coefficient table base (target digits n_i * dj + n_j)
+  int dj;
+  int16_t si, sj;  // sites (sj = -1: single-site, diagonal)
+  int8_t qi, qj;   // n_target = n_source + q
+  int8_t pad[2];
+};
+static_assert(sizeof(KSecChan) == 16, "KSecChan layout");
+
+struct KSector {
+  long long Dsec;          // retained states
+  int N, K;                // sites, digit total
+  int nch;                 // channels (all conserve the digit sum)
+  const int* d;            // [N] local dimensions
+  const long long* cnt;    // [(N + 1) * (K + 1)] cnt_k[t] at k * (K + 1) + t
+  const long long* A;      // rank tables, site k at Aoff[k]: [t * (d_k + 1) + n]
+  const int* Aoff;         // [N]
+  const KSecChan* ch;      // [nch]
+  const double* tab_d;     // coefficient pool
+  const float* tab_f;
+};
+
 // Launch choice of the apply kernel; 0 = library default for each field.
 struct TuneCfg {
   int ctas = 0;  // persistent grid size
@@ -222,6 +255,14 @@ struct Plan {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
 
+  // fixed digit-sum sector (hm_create_sector): vectors hold the Dsec
+  // retained states instead of all D
+  bool sector = false;
+  long long sec_total = 0;
+  long long Dsec = 0;
+  KSector ksec{};
+  void* sec_dev = nullptr;
+
   // merged channels of H and H^T (H^T empty when H is symmetric) and the
   // identity part, kept for building tile tables per nvec
   std::vector<Channel> chH, chT;
@@ -247,6 +288,13 @@ struct Plan {
 // plan.cpp
 int build_plan(Plan* p);            // (re)derive tables from sites/terms and upload
 void free_plan_device(Plan* p);
+
+// sector.cu
+int build_sector(Plan* p);   // sector tables from p->chH (after build_plan's host half)
+void free_sector(Plan* p);
+int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
+// length of the plan's vectors in states: D, or Dsec for a sector plan
+inline long long vec_states(const Plan* p) { return p->sector ? p->Dsec : p->D; }
 
 // tile_plan.cpp
 struct HostTile;

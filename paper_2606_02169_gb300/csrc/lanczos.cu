@@ -293,7 +293,7 @@ static std::vector<double> lowest_eigvec(const std::vector<double>& a, const std
 template <class T>
 static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, double* alpha,
                      double* beta, int* steps_done, T* psi0, double* e0, cudaStream_t s) {
-  const long long n = p->D;
+  const long long n = vec_states(p);
   const int vb = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
   const int rb = (int)std::min<long long>((n + kRedThreads - 1) / kRedThreads, kRedBlocks);
   T *V = nullptr;

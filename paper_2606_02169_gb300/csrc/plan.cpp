@@ -751,6 +751,7 @@ int build_plan(Plan* p) {
   fill(p->k, 0);
   fill(p->kt, 1);
   ++p->gen;
+  if (p->sector) return build_sector(p);
   return HM_OK;
 }
 

@@ -1,0 +1,243 @@
+// y = H x inside a fixed digit-sum sector (Sec. VI case 2; App. D): the
+// retained states are the digit tuples with sum_k n_k = K (a fixed total
+// magnetization for spins, a fixed excitation number for spin-boson models),
+// stored packed in ascending full-index order. Pull form (Sec. II): one
+// thread per packed target row F:
+//   1. unpack F to its digits by combinatorial unranking (count tables);
+//   2. for every channel, the target-digit coefficient table gives the
+//      matrix element, zero for an inadmissible source digit (Sec. IV.B);
+//   3. the source's packed index is the lookup of Sec. VI, done as a rank
+//      update: a move on sites i < j changes only the rank terms of sites
+//      i..j (KSector), so the lookup costs O(j - i + 1) table reads and
+//      cannot fail for a channel that conserves the digit sum;
+//   4. y_F accumulates coefficient * x[source] (App. D step 4).
+// Channels that do not conserve the digit sum are rejected when the plan is
+// built (their sources lie outside the sector, so the projected operator
+// would silently drop them).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace hm {
+
+constexpr int kSecNT = 256;
+
+// rank table of site k at remaining total t and digit n
+__device__ __forceinline__ long long sec_A(const KSector& S, int k, int t, int n) {
+  return __ldg(S.A + __ldg(S.Aoff + k) + t * (__ldg(S.d + k) + 1) + n);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __restrict__ x, T* __restrict__ y,
+                                                   int nvec) {
+  // per-thread digits and remaining totals (before each site), in shared memory
+  extern __shared__ unsigned char ssm[];
+  unsigned char* dig = ssm;                      // [N][blockDim]
+  unsigned char* rem = ssm + S.N * blockDim.x;   // [N][blockDim]
+  const int t = threadIdx.x;
+  const int K1 = S.K + 1;
+  for (long long F = blockIdx.x * (long long)blockDim.x + t; F < S.Dsec; F += (long long)gridDim.x * blockDim.x) {
+    // 1. unrank
+    long long r = F;
+    int left = S.K;
+    for (int k = 0; k < S.N; ++k) {
+      const long long* c = S.cnt + (long long)(k + 1) * K1;
+      int m = 0;
+      while (true) {
+        const long long cm = (left - m >= 0) ? __ldg(c + left - m) : 0LL;
+        if (r < cm) break;
+        r -= cm;
+        ++m;
+      }
+      dig[k * blockDim.x + t] = (unsigned char)m;
+      rem[k * blockDim.x + t] = (unsigned char)left;
+      left -= m;
+    }
+    // 2.-4. channels
+    using Acc = double;
+    Acc acc[8];
+    for (int v = 0; v < nvec && v < 8; ++v) acc[v] = 0.0;
+    for (int v0 = 0; v0 < nvec; v0 += 8) {
+      const int nv = min(8, nvec - v0);
+      for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+      for (int c = 0; c < S.nch; ++c) {
+        const KSecChan ch = S.ch[c];
+        const int ni = dig[ch.si * blockDim.x + t];
+        const int nj = ch.sj >= 0 ? dig[ch.sj * blockDim.x + t] : 0;
+        const double cf = __ldg(S.tab_d + ch.tab + ni * ch.dj + nj);
+        if (cf == 0.0) continue;
+        long long src = F;
+        if (ch.qi != 0 || ch.qj != 0) {
+          // rank terms of sites si..sj, target and source (sj > si)
+          const int i = ch.si, j = ch.sj, q = ch.qi;
+          long long dlt = sec_A(S, i, rem[i * blockDim.x + t], ni - q) - sec_A(S, i, rem[i * blockDim.x + t], ni);
+          for (int k = i + 1; k < j; ++k) {
+            const int rk = rem[k * blockDim.x + t], nk = dig[k * blockDim.x + t];
+            dlt += sec_A(S, k, rk + q, nk) - sec_A(S, k, rk, nk);
+          }
+          const int rj = rem[j * blockDim.x + t];
+          dlt += sec_A(S, j, rj + q, nj - ch.qj) - sec_A(S, j, rj, nj);
+          src = F + dlt;
+        }
+        const T* xs = x + src * nvec + v0;
+        for (int v = 0; v < nv; ++v) acc[v] = fma(cf, (double)xs[v], acc[v]);
+      }
+      T* ys = y + F * nvec + v0;
+      for (int v = 0; v < nv; ++v) ys[v] = (T)acc[v];
+    }
+  }
+}
+
+void free_sector(Plan* p) {
+  if (p->sec_dev) cudaFree(p->sec_dev);
+  p->sec_dev = nullptr;
+  p->ksec = KSector{};
+}
+
+int build_sector(Plan* p) {
+  const int N = p->N;
+  const long long Kl = p->sec_total;
+  long long maxsum = 0;
+  for (auto& st : p->sites) maxsum += st.dim - 1;
+  if (Kl < 0 || Kl > maxsum) {
+    set_error("digit total outside [0, sum_k (d_k - 1)]: the sector is empty");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (Kl > 255) {
+    set_error("sector digit totals above 255 are not supported");
+    return HM_ERR_UNSUPPORTED;
+  }
+  const int K = (int)Kl, K1 = K + 1;
+  // counts, with an overflow guard (Dsec < 2^62)
+  std::vector<long long> cnt((size_t)(N + 1) * K1, 0);
+  cnt[(size_t)N * K1 + 0] = 1;
+  const long long lim = (1LL << 62);
+  for (int k = N - 1; k >= 0; --k)
+    for (int t = 0; t <= K; ++t) {
+      long long s = 0;
+      for (int m = 0; m < p->sites[k].dim && m <= t; ++m) {
+        s += cnt[(size_t)(k + 1) * K1 + t - m];
+        if (s >= lim) {
+          set_error("sector dimension must be below 2^62");
+          return HM_ERR_OVERFLOW;
+        }
+      }
+      cnt[(size_t)k * K1 + t] = s;
+    }
+  const long long Dsec = cnt[K];
+  std::vector<int> dims(N), Aoff(N);
+  std::vector<long long> A;
+  for (int k = 0; k < N; ++k) {
+    dims[k] = p->sites[k].dim;
+    Aoff[k] = (int)A.size();
+    for (int t = 0; t <= K; ++t)
+      for (int n = 0; n <= dims[k]; ++n) {
+        long long s = 0;
+        for (int m = 0; m < n; ++m)
+          if (t - m >= 0) s += cnt[(size_t)(k + 1) * K1 + t - m];
+        A.push_back(s);
+      }
+  }
+  // channels: every merged channel must conserve the digit sum
+  std::vector<KSecChan> ch;
+  std::vector<double> tab;
+  std::vector<float> tabf;
+  double cst = p->constant;
+  for (const Channel& c : p->chH) {
+    bool nz = false;
+    for (auto& z : c.T) nz = nz || z != std::complex<double>(0, 0);
+    if (!nz) continue;
+    if (c.qi + (c.j >= 0 ? c.qj : 0) != 0) {
+      set_error("the term list does not conserve the sector's digit sum (a channel moves it by " +
+                std::to_string(c.qi + (c.j >= 0 ? c.qj : 0)) + ")");
+      return HM_ERR_UNSUPPORTED;
+    }
+    KSecChan k{};
+    k.tab = (int)tab.size();
+    k.dj = c.dj;
+    k.si = (int16_t)c.i;
+    k.sj = (int16_t)(c.j >= 0 ? c.j : -1);
+    k.qi = (int8_t)c.qi;
+    k.qj = (int8_t)(c.j >= 0 ? c.qj : 0);
+    for (auto& z : c.T) {
+      tab.push_back(z.real());
+      tabf.push_back((float)z.real());
+    }
+    ch.push_back(k);
+  }
+  if (cst != 0.0) {  // identity terms: a diagonal channel on site 0 with value cst
+    KSecChan k{};
+    k.tab = (int)tab.size();
+    k.dj = 1;
+    k.si = 0;
+    k.sj = -1;
+    for (int n = 0; n < dims[0]; ++n) {
+      tab.push_back(cst);
+      tabf.push_back((float)cst);
+    }
+    ch.push_back(k);
+  }
+  // upload
+  struct Sec { const void* src; size_t bytes; size_t off; };
+  std::vector<Sec> secs;
+  size_t cur = 0;
+  auto add = [&](const void* src, size_t bytes) {
+    cur = (cur + 255) & ~size_t(255);
+    secs.push_back({src, bytes, cur});
+    const size_t o = cur;
+    cur += std::max<size_t>(bytes, 1);
+    return o;
+  };
+  const size_t o_d = add(dims.data(), dims.size() * 4);
+  const size_t o_cnt = add(cnt.data(), cnt.size() * 8);
+  const size_t o_A = add(A.data(), A.size() * 8);
+  const size_t o_Aoff = add(Aoff.data(), Aoff.size() * 4);
+  const size_t o_ch = add(ch.data(), ch.size() * sizeof(KSecChan));
+  const size_t o_tab = add(tab.data(), tab.size() * 8);
+  const size_t o_tabf = add(tabf.data(), tabf.size() * 4);
+  const size_t total = (cur + 255) & ~size_t(255);
+  std::vector<unsigned char> host(total, 0);
+  for (auto& sc : secs)
+    if (sc.bytes) std::memcpy(host.data() + sc.off, sc.src, sc.bytes);
+  free_sector(p);
+  cudaError_t e = cudaMalloc(&p->sec_dev, total);
+  if (e != cudaSuccess) {
+    p->sec_dev = nullptr;
+    return cuda_fail(e, "sector tables");
+  }
+  e = cudaMemcpy(p->sec_dev, host.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "sector table upload");
+  const unsigned char* b = (const unsigned char*)p->sec_dev;
+  KSector& S = p->ksec;
+  S.Dsec = Dsec;
+  S.N = N;
+  S.K = K;
+  S.nch = (int)ch.size();
+  S.d = (const int*)(b + o_d);
+  S.cnt = (const long long*)(b + o_cnt);
+  S.A = (const long long*)(b + o_A);
+  S.Aoff = (const int*)(b + o_Aoff);
+  S.ch = (const KSecChan*)(b + o_ch);
+  S.tab_d = (const double*)(b + o_tab);
+  S.tab_f = (const float*)(b + o_tabf);
+  p->Dsec = Dsec;
+  return HM_OK;
+}
+
+int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
+  const KSector& S = p->ksec;
+  const size_t smem = (size_t)2 * S.N * kSecNT;
+  const long long need = (S.Dsec + kSecNT - 1) / kSecNT;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms() * 8));
+  if (dt == HM_F32)
+    k_sector<float><<<grid, kSecNT, smem, s>>>(S, (const float*)x, (float*)y, (int)nvec);
+  else
+    k_sector<double><<<grid, kSecNT, smem, s>>>(S, (const double*)x, (double*)y, (int)nvec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sector apply launch");
+  return HM_OK;
+}
+
+}  // namespace hm

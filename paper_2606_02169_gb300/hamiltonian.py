@@ -49,7 +49,11 @@ class Hamiltonian:
     op names as in include/hm.h ("Sz", "Sx", "Sy", "Sp", "Sm", "Sz2", "Sp2",
     "Sm2", "N", "a", "adag", "I")."""
 
-    def __init__(self, sites, terms):
+    def __init__(self, sites, terms, sector_total=None):
+        """sector_total: None for the full product basis, else the fixed sum of
+        the local digits n_k = m_k + s_k (a fixed-magnetization or
+        excitation-number sector, hm_create_sector); D is then the number of
+        retained states and vectors hold only those."""
         self._lib = C.load()
         torch.cuda.init()
         self.sites = [(_site_kind(k), int(d)) for k, d in sites]
@@ -57,7 +61,12 @@ class Hamiltonian:
         cs = (C.hm_site * len(self.sites))(*[C.hm_site(k, d) for k, d in self.sites])
         ts = (C.hm_term * max(1, len(self.terms)))(*[C.hm_term(i, oi, j, oj, c) for i, oi, j, oj, c in self.terms])
         h = ctypes.c_void_p()
-        C.check(self._lib.hm_create(cs, len(self.sites), ts, len(self.terms), ctypes.byref(h)), "hm_create")
+        self.sector_total = sector_total
+        if sector_total is None:
+            C.check(self._lib.hm_create(cs, len(self.sites), ts, len(self.terms), ctypes.byref(h)), "hm_create")
+        else:
+            C.check(self._lib.hm_create_sector(cs, len(self.sites), ts, len(self.terms), int(sector_total),
+                                               ctypes.byref(h)), "hm_create_sector")
         self._h = h
         self.D = int(self._lib.hm_dim(h))
         self.nterms = len(self.terms)
