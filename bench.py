@@ -8,8 +8,9 @@ exceed the 129 MB L2, so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0). Extra keys report the other forms of the path
 against this plain FP64 kernel: FP32 storage, the 1.07e9-state
-Tavis-Cummings apply, the batched persistent launch, the adjoint, and the
-Lanczos ground-state energy in FP32 vs FP64 storage.
+Tavis-Cummings apply, the batched persistent launch, the adjoint, the
+Lanczos ground-state energy in FP32 vs FP64 storage, the paper's Table I
+models, and a fixed-magnetization sector beside the full basis.
 
 --impl reference times the CPU oracle (the reference arm of this build) on
 a bounded sample of the same workload, on the host cores.
@@ -19,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -455,6 +457,7 @@ def run_ours(args):
 
 
 def variants(args, h, m, x, y, ms_f64, stream, hbm):
+    import numpy as np
     import torch
 
     import workloads as W
@@ -557,6 +560,44 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
                      "note": "paper figure: Table I, CPU unstated; context only"}
         del hc, xc, yc
         torch.cuda.empty_cache()
+
+    # fixed-magnetization sector (packed basis, combinatorial lookup): the
+    # periodic Heisenberg chain N=30, M=0 (C(30,15) = 1.55e8 of 2^30 states),
+    # FP64, beside the full-basis apply of the same chain and the sector
+    # oracle's case-2 restatement on a bounded sample of rows
+    ns = 30
+    ss = [("spin", 2)] * ns
+    st = []
+    for i in range(ns):
+        j = (i + 1) % ns
+        st += [(i, "Sp", j, "Sm", 0.5), (i, "Sm", j, "Sp", 0.5), (i, "Sz", j, "Sz", 1.0)]
+    hs = Hamiltonian(ss, st, sector_total=ns // 2)
+    xs_ = W.torch_vector(hs.D, 21, dtype=torch.float64)
+    ys_ = torch.empty_like(xs_)
+    k = 5
+    ms_s = timed(lambda: hs.apply(xs_, out=ys_), k, 2, 1, stream) / k
+    import oracle
+    rows = np.arange(2000) * (hs.D // 2000)
+    xh = xs_.cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.sector_rows(ss, st, ns // 2, xh, rows)
+    t_or = time.perf_counter() - t0
+    del hs, xs_, ys_
+    torch.cuda.empty_cache()
+    hf = Hamiltonian(ss, st)
+    if args.tune:
+        hf.tune(1, torch.float64)
+    xf_ = W.torch_vector(hf.D, 22, dtype=torch.float64)
+    yf_ = torch.empty_like(xf_)
+    ms_f = timed(lambda: hf.apply(xf_, out=yf_), k, 2, 1, stream) / k
+    out["sector_chain_n30_m0_f64"] = {
+        "Dsec": math.comb(ns, ns // 2), "ms": ms_s, "gstates_s": math.comb(ns, ns // 2) / ms_s / 1e6,
+        "hbm_frac_algorithmic": 16 * math.comb(ns, ns // 2) / ms_s / 1e6 / hbm,
+        "full_basis_ms": ms_f, "full_basis_gstates_s": hf.D / ms_f / 1e6,
+        "vector_bytes_sector_vs_full": math.comb(ns, ns // 2) / hf.D,
+        "cpu_oracle_rows_per_s": rows.size / t_or, "cpu_oracle_sample": f"{rows.size} rows, Python case-2 restatement"}
+    del hf, xf_, yf_
+    torch.cuda.empty_cache()
 
     # adjoint on the 4x5 lattice (D = 2^20, FP64): H^T gy + 113 coupling gradients
     ml = W.square_lattice_xxz(4, 5, seed=4)

@@ -198,7 +198,7 @@ struct KSector {
   long long Dsec;          // retained states
   int N, K;                // sites, digit total
   int nch;                 // channels (all conserve the digit sum)
-  const int* d;            // [N] local dimensions
+  const int* d;            // [N] local dimensions capped at K + 1 (rank-table strides)
   const long long* cnt;    // [(N + 1) * (K + 1)] cnt_k[t] at k * (K + 1) + t
   const long long* A;      // rank tables, site k at Aoff[k]: [t * (d_k + 1) + n]
   const int* Aoff;         // [N]
@@ -262,6 +262,7 @@ struct Plan {
   long long Dsec = 0;
   KSector ksec{};
   void* sec_dev = nullptr;
+  long long sec_nA = 0, sec_ntab = 0;   // rank-table and coefficient-pool lengths
 
   // merged channels of H and H^T (H^T empty when H is symmetric) and the
   // identity part, kept for building tile tables per nvec

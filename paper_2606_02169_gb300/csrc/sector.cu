@@ -23,30 +23,62 @@
 namespace hm {
 
 constexpr int kSecNT = 256;
+constexpr size_t kSecTablesMax = 96 * 1024;  // tables staged in shared memory up to this size
 
-// rank table of site k at remaining total t and digit n
-__device__ __forceinline__ long long sec_A(const KSector& S, int k, int t, int n) {
-  return __ldg(S.A + __ldg(S.Aoff + k) + t * (__ldg(S.d + k) + 1) + n);
+// Table pointers of one launch (shared-memory copies, or the global tables).
+struct SecTabs {
+  const int* d;
+  const long long* cnt;
+  const long long* A;
+  const int* Aoff;
+  const KSecChan* ch;
+  const double* tab;
+};
+
+__host__ __device__ inline size_t sec_align(size_t b) { return (b + 15) & ~size_t(15); }
+
+// bytes of the staged tables (host and device agree on the layout)
+__host__ __device__ inline size_t sec_tables_bytes(int N, int K, long long nA, int nch, long long ntab) {
+  return sec_align((size_t)N * 4) + sec_align((size_t)(N + 1) * (K + 1) * 8) + sec_align((size_t)nA * 8) +
+         sec_align((size_t)N * 4) + sec_align((size_t)nch * sizeof(KSecChan)) + sec_align((size_t)ntab * 8);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __restrict__ x, T* __restrict__ y,
-                                                   int nvec) {
-  // per-thread digits and remaining totals (before each site), in shared memory
-  extern __shared__ unsigned char ssm[];
-  unsigned char* dig = ssm;                      // [N][blockDim]
-  unsigned char* rem = ssm + S.N * blockDim.x;   // [N][blockDim]
+                                                   int nvec, long long nA, long long ntab, int staged) {
+  extern __shared__ __align__(16) unsigned char ssm[];
+  const int N = S.N, K1 = S.K + 1;
+  SecTabs G{S.d, S.cnt, S.A, S.Aoff, S.ch, S.tab_d};
+  size_t o = 0;
+  if (staged) {  // copy the tables once per CTA
+    int* d = (int*)(ssm + o);            o += sec_align((size_t)N * 4);
+    long long* cnt = (long long*)(ssm + o); o += sec_align((size_t)(N + 1) * K1 * 8);
+    long long* A = (long long*)(ssm + o);   o += sec_align((size_t)nA * 8);
+    int* Aoff = (int*)(ssm + o);          o += sec_align((size_t)N * 4);
+    KSecChan* ch = (KSecChan*)(ssm + o);  o += sec_align((size_t)S.nch * sizeof(KSecChan));
+    double* tab = (double*)(ssm + o);     o += sec_align((size_t)ntab * 8);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) { d[i] = S.d[i]; Aoff[i] = S.Aoff[i]; }
+    for (int i = threadIdx.x; i < (N + 1) * K1; i += blockDim.x) cnt[i] = S.cnt[i];
+    for (long long i = threadIdx.x; i < nA; i += blockDim.x) A[i] = S.A[i];
+    for (int i = threadIdx.x; i < S.nch; i += blockDim.x) ch[i] = S.ch[i];
+    for (long long i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = S.tab_d[i];
+    G = SecTabs{d, cnt, A, Aoff, ch, tab};
+    __syncthreads();
+  }
+  // per-thread digits and remaining totals (before each site)
+  unsigned char* dig = ssm + o;                    // [N][blockDim]
+  unsigned char* rem = dig + N * blockDim.x;       // [N][blockDim]
   const int t = threadIdx.x;
-  const int K1 = S.K + 1;
+  auto Aat = [&](int k, int tt, int n) { return G.A[G.Aoff[k] + tt * (G.d[k] + 1) + n]; };
   for (long long F = blockIdx.x * (long long)blockDim.x + t; F < S.Dsec; F += (long long)gridDim.x * blockDim.x) {
     // 1. unrank
     long long r = F;
     int left = S.K;
-    for (int k = 0; k < S.N; ++k) {
-      const long long* c = S.cnt + (long long)(k + 1) * K1;
+    for (int k = 0; k < N; ++k) {
+      const long long* c = G.cnt + (k + 1) * K1;
       int m = 0;
       while (true) {
-        const long long cm = (left - m >= 0) ? __ldg(c + left - m) : 0LL;
+        const long long cm = (left - m >= 0) ? c[left - m] : 0LL;
         if (r < cm) break;
         r -= cm;
         ++m;
@@ -55,37 +87,39 @@ __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __r
       rem[k * blockDim.x + t] = (unsigned char)left;
       left -= m;
     }
-    // 2.-4. channels
-    using Acc = double;
-    Acc acc[8];
-    for (int v = 0; v < nvec && v < 8; ++v) acc[v] = 0.0;
+    // 2.-4. channels, up to 8 right-hand sides per pass; the diagonal
+    // channels' coefficients are summed first and multiply x_F once
     for (int v0 = 0; v0 < nvec; v0 += 8) {
       const int nv = min(8, nvec - v0);
+      double acc[8];
       for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+      double dsum = 0.0;
       for (int c = 0; c < S.nch; ++c) {
-        const KSecChan ch = S.ch[c];
+        const KSecChan ch = G.ch[c];
         const int ni = dig[ch.si * blockDim.x + t];
         const int nj = ch.sj >= 0 ? dig[ch.sj * blockDim.x + t] : 0;
-        const double cf = __ldg(S.tab_d + ch.tab + ni * ch.dj + nj);
+        const double cf = G.tab[ch.tab + ni * ch.dj + nj];
         if (cf == 0.0) continue;
-        long long src = F;
-        if (ch.qi != 0 || ch.qj != 0) {
-          // rank terms of sites si..sj, target and source (sj > si)
-          const int i = ch.si, j = ch.sj, q = ch.qi;
-          long long dlt = sec_A(S, i, rem[i * blockDim.x + t], ni - q) - sec_A(S, i, rem[i * blockDim.x + t], ni);
-          for (int k = i + 1; k < j; ++k) {
-            const int rk = rem[k * blockDim.x + t], nk = dig[k * blockDim.x + t];
-            dlt += sec_A(S, k, rk + q, nk) - sec_A(S, k, rk, nk);
-          }
-          const int rj = rem[j * blockDim.x + t];
-          dlt += sec_A(S, j, rj + q, nj - ch.qj) - sec_A(S, j, rj, nj);
-          src = F + dlt;
+        if (ch.qi == 0 && ch.qj == 0) {
+          dsum += cf;
+          continue;
         }
-        const T* xs = x + src * nvec + v0;
+        // rank terms of sites si..sj, target and source (sj > si)
+        const int i = ch.si, j = ch.sj, q = ch.qi;
+        const int ri = rem[i * blockDim.x + t];
+        long long dlt = Aat(i, ri, ni - q) - Aat(i, ri, ni);
+        for (int k = i + 1; k < j; ++k) {
+          const int rk = rem[k * blockDim.x + t], nk = dig[k * blockDim.x + t];
+          dlt += Aat(k, rk + q, nk) - Aat(k, rk, nk);
+        }
+        const int rj = rem[j * blockDim.x + t];
+        dlt += Aat(j, rj + q, nj - ch.qj) - Aat(j, rj, nj);
+        const T* xs = x + (F + dlt) * nvec + v0;
         for (int v = 0; v < nv; ++v) acc[v] = fma(cf, (double)xs[v], acc[v]);
       }
+      const T* xo = x + F * nvec + v0;
       T* ys = y + F * nvec + v0;
-      for (int v = 0; v < nv; ++v) ys[v] = (T)acc[v];
+      for (int v = 0; v < nv; ++v) ys[v] = (T)fma(dsum, (double)xo[v], acc[v]);
     }
   }
 }
@@ -130,7 +164,8 @@ int build_sector(Plan* p) {
   std::vector<int> dims(N), Aoff(N);
   std::vector<long long> A;
   for (int k = 0; k < N; ++k) {
-    dims[k] = p->sites[k].dim;
+    // a digit above K cannot occur in the sector: the rank tables stop at K + 1
+    dims[k] = std::min(p->sites[k].dim, K + 1);
     Aoff[k] = (int)A.size();
     for (int t = 0; t <= K; ++t)
       for (int n = 0; n <= dims[k]; ++n) {
@@ -223,18 +258,27 @@ int build_sector(Plan* p) {
   S.tab_d = (const double*)(b + o_tab);
   S.tab_f = (const float*)(b + o_tabf);
   p->Dsec = Dsec;
+  p->sec_nA = (long long)A.size();
+  p->sec_ntab = (long long)tab.size();
   return HM_OK;
 }
 
 int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
   const KSector& S = p->ksec;
-  const size_t smem = (size_t)2 * S.N * kSecNT;
+  const size_t tabs = sec_tables_bytes(S.N, S.K, p->sec_nA, S.nch, p->sec_ntab);
+  const int staged = tabs <= kSecTablesMax;
+  const size_t smem = (staged ? tabs : 0) + (size_t)2 * S.N * kSecNT;
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_sector<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sector<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   const long long need = (S.Dsec + kSecNT - 1) / kSecNT;
   const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms() * 8));
   if (dt == HM_F32)
-    k_sector<float><<<grid, kSecNT, smem, s>>>(S, (const float*)x, (float*)y, (int)nvec);
+    k_sector<float><<<grid, kSecNT, smem, s>>>(S, (const float*)x, (float*)y, (int)nvec, p->sec_nA, p->sec_ntab, staged);
   else
-    k_sector<double><<<grid, kSecNT, smem, s>>>(S, (const double*)x, (double*)y, (int)nvec);
+    k_sector<double><<<grid, kSecNT, smem, s>>>(S, (const double*)x, (double*)y, (int)nvec, p->sec_nA, p->sec_ntab,
+                                                staged);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sector apply launch");
   return HM_OK;
