@@ -16,9 +16,12 @@
  * Vectors: caller-owned DEVICE pointers, state-major interleaved: element v
  * of state k is at [k*nvec + v]. Real storage only (HM_F64 / HM_F32).
  * Every call is asynchronous on the given CUDA stream (NULL = legacy default
- * stream) unless stated otherwise. Plans are library-owned; a plan may be used
- * from several streams at once, but hm_set_coefficients must not overlap
- * applies of the same plan.
+ * stream) unless stated otherwise. Plans are library-owned. Applies of one
+ * plan (hm_apply, hm_batch_apply) may run on several streams at once: the
+ * FP64 input split takes per-call scratch (see hm_apply), and hm_lanczos
+ * allocates its own vectors. Adjoint passes share a plan-owned reduction
+ * buffer, so adjoint calls of one plan must not overlap on the GPU.
+ * hm_set_coefficients must not overlap any call of the same plan.
  *
  * Errors: every int-returning call returns HM_OK (0) or a negative HM_ERR_*;
  * hm_strerror() names a code and hm_last_error() returns a thread-local text
@@ -101,7 +104,7 @@ int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_
  * sum (else HM_ERR_UNSUPPORTED); digit_total outside [0, sum_k (d_k - 1)]
  * gives HM_ERR_INVALID_ARG, above 255 HM_ERR_UNSUPPORTED. hm_apply,
  * hm_set_coefficients, hm_lanczos, hm_dim, hm_num_terms and hm_destroy
- * accept sector plans (apply arithmetic: FP64 accumulation for both dtypes);
+ * accept sector plans (arithmetic as in hm_apply);
  * hm_apply_ex, hm_apply_adjoint, hm_coupling_gradients_static, hm_tune and
  * batches return HM_ERR_UNSUPPORTED. */
 int hm_create_sector(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
@@ -120,7 +123,11 @@ int32_t hm_num_terms(hm_handle h);
 /* y = H x for nvec right-hand sides (x, y: device, D*nvec elements of dtype;
  * x read-only, y fully overwritten; x and y must not overlap). Each output
  * element is owned by exactly one GPU lane (pull form, Sec. II): no atomics,
- * bit-reproducible run to run. */
+ * bit-reproducible run to run. HM_F64 first splits x into D*nvec float
+ * pairs of stream-ordered scratch from a library memory pool per device,
+ * released on the same stream after the apply; the pool keeps freed memory
+ * for later calls (hm_destroy hands the unused part back). Inside a stream
+ * capture the scratch becomes the graph's own allocation. */
 int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* Diagnostic variant of hm_apply (it ignores hm_tune's choice). flags
@@ -144,11 +151,10 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
  *                  nterms doubles, overwritten), O_t = op_i op_j without coef.
  * gy, x: device vectors of dtype. gcoef is always FP64, reduced
  * deterministically (fixed-order two-pass reduction, no atomics). Uses
- * library-owned scratch of O(nterms * grid) doubles per plan and, for
- * HM_F64 gradients, two plan-owned buffers of D*nvec float pairs (gy and x
- * split once); all grow on demand, so the first call of a size should come
- * before any stream capture. Calls on the same plan must not overlap on the
- * GPU. */
+ * plan-owned scratch of O(nterms * grid) doubles, grown on demand (so the
+ * first call of a size should come before any stream capture) and, for
+ * HM_F64, per-call pool scratch as in hm_apply for gy and x split once.
+ * Calls on the same plan must not overlap on the GPU. */
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
                      int64_t nvec, hm_dtype dtype, void* stream);
 

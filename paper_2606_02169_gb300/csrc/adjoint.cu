@@ -230,8 +230,9 @@ int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gco
   }
   if (dt == HM_F64) {  // split gy and x once instead of at every gather
     const float2 *gs = nullptr, *xs = nullptr;
-    int rc = split_vector(p, 1, gy, p->D * nvec, s, &gs);
-    if (rc == HM_OK) rc = split_vector(p, 0, x, p->D * nvec, s, &xs);
+    Scratch gsb, xsb;
+    int rc = split_vector(gy, p->D * nvec, s, gsb, &gs);
+    if (rc == HM_OK) rc = split_vector(x, p->D * nvec, s, xsb, &xs);
     if (rc) return rc;
     return launch_term_grad_split(p, gs, xs, gcoef, nvec, (double*)p->scratch, grid, s);
   }

@@ -3,6 +3,8 @@
 // apply_kernel.cuh and are instantiated per arithmetic policy in
 // apply_f32.cu / apply_df64.cu / apply_f64.cu.
 #include <algorithm>
+#include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "apply_kernel.cuh"
@@ -48,34 +50,58 @@ __global__ void __launch_bounds__(256) k_split_f64_scalar(const double* __restri
     xs[i] = split_f64(__ldcs(x + i));
 }
 
-// Plan-owned device buffer grown on demand (stream-ordered: the previous
-// users of the old buffer on `s` finish before it is freed).
-static void* grow_buffer(void*& buf, size_t& cap, size_t bytes, cudaStream_t s, int* rc) {
-  if (cap >= bytes) return buf;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cs);
-  if (cs != cudaStreamCaptureStatusNone) {
-    set_error("FP64 apply needs its split buffer grown: run it once before stream capture");
-    *rc = HM_ERR_INVALID_ARG;
-    return nullptr;
+// FP64 inputs are split into float pairs in per-call scratch from one
+// library pool per device whose release threshold keeps its memory: calls of
+// one plan on different streams get separate buffers, and inside a stream
+// capture the allocation and release become the graph's own memory nodes.
+constexpr int kMaxDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[kMaxDevices] = {};
+
+static cudaError_t scratch_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    cudaMemPool_t m = nullptr;
+    e = cudaMemPoolCreate(&m, &pp);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(m, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(m);
+      return e;
+    }
+    g_pool[dev] = m;
   }
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && buf) e = cudaFree(buf);
-  buf = nullptr;
-  cap = 0;
-  if (e == cudaSuccess) e = cudaMalloc(&buf, bytes);
-  if (e != cudaSuccess) {
-    buf = nullptr;
-    *rc = cuda_fail(e, "FP64 split buffer");
-    return nullptr;
-  }
-  cap = bytes;
-  return buf;
+  *out = g_pool[dev];
+  return cudaSuccess;
 }
 
-// the split input of the apply
-static void* split_buffer(Plan* p, size_t bytes, cudaStream_t s, int* rc) {
-  return grow_buffer(p->xsplit, p->xsplit_bytes, bytes, s, rc);
+int scratch_alloc(Scratch& b, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t m = nullptr;
+  cudaError_t e = scratch_pool(&m);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&b.ptr, std::max<size_t>(bytes, 16), m, s);
+  if (e != cudaSuccess) {
+    b.ptr = nullptr;
+    return cuda_fail(e, "FP64 split scratch");
+  }
+  b.s = s;
+  return HM_OK;
+}
+
+// hand the pools' unused memory back (allocations still queued keep theirs)
+void scratch_trim() {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  for (cudaMemPool_t m : g_pool)
+    if (m) cudaMemPoolTrimTo(m, 0);
 }
 
 cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
@@ -87,16 +113,12 @@ cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// n FP64 values split into the plan's buffer `which` (0: the apply's, 1: a
-// second one), for kernels that read both gy and x split.
-int split_vector(Plan* p, int which, const void* x, long long n, cudaStream_t s, const float2** out) {
-  int rc = HM_OK;
-  void* buf = which == 0 ? split_buffer(p, (size_t)n * sizeof(float2), s, &rc)
-                         : grow_buffer(p->gsplit, p->gsplit_bytes, (size_t)n * sizeof(float2), s, &rc);
-  if (!buf) return rc;
-  cudaError_t e = split_into(x, buf, n, s);
+int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out) {
+  int rc = scratch_alloc(b, (size_t)n * sizeof(float2), s);
+  if (rc) return rc;
+  cudaError_t e = split_into(x, b.ptr, n, s);
   if (e != cudaSuccess) return cuda_fail(e, "FP64 split launch");
-  *out = (const float2*)buf;
+  *out = (const float2*)b.ptr;
   return HM_OK;
 }
 
@@ -118,13 +140,11 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
   if (cfg.kern == 2) gcfg = TuneCfg{};
   cudaError_t e;
   const void* xin = x;
+  Scratch xsb;
   if (dt == HM_F64 && !native_f64) {
-    int rc = HM_OK;
-    const long long n = p->D * nvec;
-    void* xs = split_buffer(p, (size_t)n * sizeof(float2), s, &rc);
-    if (!xs) return rc;
-    e = split_into(x, xs, n, s);
-    if (e != cudaSuccess) return cuda_fail(e, "FP64 split launch");
+    const float2* xs = nullptr;
+    int rc = split_vector(x, p->D * nvec, s, xsb, &xs);
+    if (rc) return rc;
     xin = xs;
   }
   e = cudaErrorInvalidConfiguration;
@@ -171,6 +191,22 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
   std::vector<const Plan*> mem;
   std::vector<const void*> sx;
   std::vector<void*> sy;
+  // FP64: the queue members' inputs are split into one scratch allocation
+  Scratch xsb;
+  std::vector<size_t> at(b->members.size(), 0);
+  if (dt == HM_F64) {
+    size_t total = 0;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+      const Plan* p = b->members[i];
+      if (fills_gpu(p, nvec)) continue;
+      at[i] = total;
+      total += ((size_t)(p->D * nvec) * sizeof(float2) + 255) & ~size_t(255);
+    }
+    if (total) {
+      int rc = scratch_alloc(xsb, total, s);
+      if (rc) return rc;
+    }
+  }
   for (size_t i = 0; i < b->members.size(); ++i) {
     Plan* p = b->members[i];
     if (fills_gpu(p, nvec)) {
@@ -183,10 +219,7 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
     if (dt == HM_F32) {
       sx.push_back(xs[i]);
     } else {
-      // each member's FP64 input is split into that member's buffer first
-      int rc = HM_OK;
-      void* buf = split_buffer(p, (size_t)(p->D * nvec) * sizeof(float2), s, &rc);
-      if (!buf) return rc;
+      void* buf = (char*)xsb.ptr + at[i];
       cudaError_t e = split_into(xs[i], buf, p->D * nvec, s);
       if (e != cudaSuccess) return cuda_fail(e, "batch split");
       sx.push_back(buf);

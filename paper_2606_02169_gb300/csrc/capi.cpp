@@ -295,10 +295,9 @@ int hm_destroy(hm_handle h) {
   free_tiles(p);
   free_sector(p);
   if (p->scratch) cudaFree(p->scratch);
-  if (p->xsplit) cudaFree(p->xsplit);
-  if (p->gsplit) cudaFree(p->gsplit);
   p->magic = 0;
   delete p;
+  scratch_trim();
   return HM_OK;
 }
 

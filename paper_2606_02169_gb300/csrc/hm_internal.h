@@ -205,6 +205,7 @@ struct KSector {
   const KSecChan* ch;      // [nch]
   const double* tab_d;     // coefficient pool
   const float* tab_f;
+  const float2* tab_df;    // as float pairs (double-float arithmetic)
 };
 
 // Launch choice of the apply kernel; 0 = library default for each field.
@@ -243,13 +244,6 @@ struct Plan {
   KPlan kt{};   // H^T (shares k's tables when H is symmetric)
   void* dev = nullptr;        // one device allocation holding every table
   size_t dev_bytes = 0;
-
-  // FP64 input split into float pairs, one vector (grown on demand); a second
-  // buffer for kernels that read two split vectors (the gradients' gy)
-  void* xsplit = nullptr;
-  size_t xsplit_bytes = 0;
-  void* gsplit = nullptr;
-  size_t gsplit_bytes = 0;
 
   // scratch for the adjoint reduction (grown on demand)
   void* scratch = nullptr;
@@ -318,7 +312,23 @@ int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, c
 int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64);
 TuneCfg tuned_cfg(Plan* p, hm_dtype dt, long long nvec);
-int split_vector(Plan* p, int which, const void* x, long long n, cudaStream_t s, const float2** out);
+// Stream-ordered device scratch from a library-owned pool that keeps its
+// memory between calls; released on the same stream when the owner goes out
+// of scope (after the launches that read it were queued).
+struct Scratch {
+  void* ptr = nullptr;
+  cudaStream_t s = nullptr;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    if (ptr) cudaFreeAsync(ptr, s);
+  }
+};
+int scratch_alloc(Scratch& b, size_t bytes, cudaStream_t s);
+void scratch_trim();
+// n FP64 values split into float pairs in fresh scratch `b`
+int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
 int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,

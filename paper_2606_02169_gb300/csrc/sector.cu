@@ -11,7 +11,8 @@
 //      i..j (KSector), so the lookup costs O(j - i + 1) table reads and
 //      cannot fail for a channel that conserves the digit sum;
 //   4. y_F accumulates coefficient * x[source] (App. D step 4).
-// Channels that do not conserve the digit sum are rejected when the plan is
+// Arithmetic as in the full-basis kernel (FP32, or double-float for FP64
+// storage). Channels that do not conserve the digit sum are rejected when the plan is
 // built (their sources lie outside the sector, so the projected operator
 // would silently drop them).
 #include <algorithm>
@@ -26,29 +27,66 @@ constexpr int kSecNT = 256;
 constexpr size_t kSecTablesMax = 96 * 1024;  // tables staged in shared memory up to this size
 
 // Table pointers of one launch (shared-memory copies, or the global tables).
+template <class C>
 struct SecTabs {
   const int* d;
   const long long* cnt;
   const long long* A;
   const int* Aoff;
   const KSecChan* ch;
-  const double* tab;
+  const C* tab;
 };
 
 __host__ __device__ inline size_t sec_align(size_t b) { return (b + 15) & ~size_t(15); }
 
 // bytes of the staged tables (host and device agree on the layout)
-__host__ __device__ inline size_t sec_tables_bytes(int N, int K, long long nA, int nch, long long ntab) {
+__host__ __device__ inline size_t sec_tables_bytes(int N, int K, long long nA, int nch, long long ntab, size_t csize) {
   return sec_align((size_t)N * 4) + sec_align((size_t)(N + 1) * (K + 1) * 8) + sec_align((size_t)nA * 8) +
-         sec_align((size_t)N * 4) + sec_align((size_t)nch * sizeof(KSecChan)) + sec_align((size_t)ntab * 8);
+         sec_align((size_t)N * 4) + sec_align((size_t)nch * sizeof(KSecChan)) + sec_align((size_t)ntab * csize);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __restrict__ x, T* __restrict__ y,
-                                                   int nvec, long long nA, long long ntab, int staged) {
+// Arithmetic of the sector kernel, as in the full-basis kernel: FP32 storage
+// in FP32; FP64 storage as double-float sums on the FP32 pipe of the input
+// split once into float pairs (GB300 runs FP64 at ~1/70 of the FP32 rate).
+template <int AR> struct SecAr;
+template <> struct SecAr<AR_F32> {
+  using TX = float;
+  using TY = float;
+  using C = float;
+  using Acc = float;
+  __device__ static const C* tab(const KSector& S) { return S.tab_f; }
+  __device__ static bool nz(C c) { return c != 0.0f; }
+  __device__ static Acc zero() { return 0.0f; }
+  __device__ static void add(Acc& a, C c) { a = __fadd_rn(a, c); }
+  __device__ static void fma(Acc& a, C c, TX x) { a = __fmaf_rn(c, x, a); }
+  __device__ static TY out(Acc hop, Acc d, TX xo) { return __fmaf_rn(d, xo, hop); }
+};
+template <> struct SecAr<AR_DF64> {
+  using TX = float2;
+  using TY = double;
+  using C = float2;
+  using Acc = DF;
+  __device__ static const C* tab(const KSector& S) { return S.tab_df; }
+  __device__ static bool nz(C c) { return c.x != 0.0f; }
+  __device__ static Acc zero() { return DF{0.f, 0.f}; }
+  __device__ static void add(Acc& a, C c) { df_add(a, c); }
+  __device__ static void fma(Acc& a, C c, TX x) { df_fma(a, c, x.x, x.y); }
+  __device__ static TY out(Acc hop, Acc d, TX xo) {
+    df_fma(hop, df_norm(d), xo.x, xo.y);
+    return df_to_double(hop);
+  }
+};
+
+template <int AR>
+__global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const typename SecAr<AR>::TX* __restrict__ x,
+                                                   typename SecAr<AR>::TY* __restrict__ y, int nvec, long long nA,
+                                                   long long ntab, int staged) {
+  using P = SecAr<AR>;
+  using C = typename P::C;
+  using TX = typename P::TX;
   extern __shared__ __align__(16) unsigned char ssm[];
   const int N = S.N, K1 = S.K + 1;
-  SecTabs G{S.d, S.cnt, S.A, S.Aoff, S.ch, S.tab_d};
+  SecTabs<C> G{S.d, S.cnt, S.A, S.Aoff, S.ch, P::tab(S)};
   size_t o = 0;
   if (staged) {  // copy the tables once per CTA
     int* d = (int*)(ssm + o);            o += sec_align((size_t)N * 4);
@@ -56,13 +94,13 @@ __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __r
     long long* A = (long long*)(ssm + o);   o += sec_align((size_t)nA * 8);
     int* Aoff = (int*)(ssm + o);          o += sec_align((size_t)N * 4);
     KSecChan* ch = (KSecChan*)(ssm + o);  o += sec_align((size_t)S.nch * sizeof(KSecChan));
-    double* tab = (double*)(ssm + o);     o += sec_align((size_t)ntab * 8);
+    C* tab = (C*)(ssm + o);               o += sec_align((size_t)ntab * sizeof(C));
     for (int i = threadIdx.x; i < N; i += blockDim.x) { d[i] = S.d[i]; Aoff[i] = S.Aoff[i]; }
     for (int i = threadIdx.x; i < (N + 1) * K1; i += blockDim.x) cnt[i] = S.cnt[i];
     for (long long i = threadIdx.x; i < nA; i += blockDim.x) A[i] = S.A[i];
     for (int i = threadIdx.x; i < S.nch; i += blockDim.x) ch[i] = S.ch[i];
-    for (long long i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = S.tab_d[i];
-    G = SecTabs{d, cnt, A, Aoff, ch, tab};
+    for (long long i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = P::tab(S)[i];
+    G = SecTabs<C>{d, cnt, A, Aoff, ch, tab};
     __syncthreads();
   }
   // per-thread digits and remaining totals (before each site)
@@ -91,17 +129,17 @@ __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __r
     // channels' coefficients are summed first and multiply x_F once
     for (int v0 = 0; v0 < nvec; v0 += 8) {
       const int nv = min(8, nvec - v0);
-      double acc[8];
-      for (int v = 0; v < nv; ++v) acc[v] = 0.0;
-      double dsum = 0.0;
+      typename P::Acc acc[8];
+      for (int v = 0; v < nv; ++v) acc[v] = P::zero();
+      typename P::Acc dsum = P::zero();
       for (int c = 0; c < S.nch; ++c) {
         const KSecChan ch = G.ch[c];
         const int ni = dig[ch.si * blockDim.x + t];
         const int nj = ch.sj >= 0 ? dig[ch.sj * blockDim.x + t] : 0;
-        const double cf = G.tab[ch.tab + ni * ch.dj + nj];
-        if (cf == 0.0) continue;
+        const C cf = G.tab[ch.tab + ni * ch.dj + nj];
+        if (!P::nz(cf)) continue;
         if (ch.qi == 0 && ch.qj == 0) {
-          dsum += cf;
+          P::add(dsum, cf);
           continue;
         }
         // rank terms of sites si..sj, target and source (sj > si)
@@ -114,12 +152,12 @@ __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const T* __r
         }
         const int rj = rem[j * blockDim.x + t];
         dlt += Aat(j, rj + q, nj - ch.qj) - Aat(j, rj, nj);
-        const T* xs = x + (F + dlt) * nvec + v0;
-        for (int v = 0; v < nv; ++v) acc[v] = fma(cf, (double)xs[v], acc[v]);
+        const TX* xs = x + (F + dlt) * nvec + v0;
+        for (int v = 0; v < nv; ++v) P::fma(acc[v], cf, xs[v]);
       }
-      const T* xo = x + F * nvec + v0;
-      T* ys = y + F * nvec + v0;
-      for (int v = 0; v < nv; ++v) ys[v] = (T)fma(dsum, (double)xo[v], acc[v]);
+      const TX* xo = x + F * nvec + v0;
+      typename P::TY* ys = y + F * nvec + v0;
+      for (int v = 0; v < nv; ++v) ys[v] = P::out(acc[v], dsum, xo[v]);
     }
   }
 }
@@ -179,6 +217,11 @@ int build_sector(Plan* p) {
   std::vector<KSecChan> ch;
   std::vector<double> tab;
   std::vector<float> tabf;
+  std::vector<float2> tabdf;
+  auto split2 = [](double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
   double cst = p->constant;
   for (const Channel& c : p->chH) {
     bool nz = false;
@@ -199,6 +242,7 @@ int build_sector(Plan* p) {
     for (auto& z : c.T) {
       tab.push_back(z.real());
       tabf.push_back((float)z.real());
+      tabdf.push_back(split2(z.real()));
     }
     ch.push_back(k);
   }
@@ -208,9 +252,10 @@ int build_sector(Plan* p) {
     k.dj = 1;
     k.si = 0;
     k.sj = -1;
-    for (int n = 0; n < dims[0]; ++n) {
+    for (int n = 0; n < p->sites[0].dim; ++n) {
       tab.push_back(cst);
       tabf.push_back((float)cst);
+      tabdf.push_back(split2(cst));
     }
     ch.push_back(k);
   }
@@ -232,6 +277,7 @@ int build_sector(Plan* p) {
   const size_t o_ch = add(ch.data(), ch.size() * sizeof(KSecChan));
   const size_t o_tab = add(tab.data(), tab.size() * 8);
   const size_t o_tabf = add(tabf.data(), tabf.size() * 4);
+  const size_t o_tabdf = add(tabdf.data(), tabdf.size() * 8);
   const size_t total = (cur + 255) & ~size_t(255);
   std::vector<unsigned char> host(total, 0);
   for (auto& sc : secs)
@@ -257,29 +303,39 @@ int build_sector(Plan* p) {
   S.ch = (const KSecChan*)(b + o_ch);
   S.tab_d = (const double*)(b + o_tab);
   S.tab_f = (const float*)(b + o_tabf);
+  S.tab_df = (const float2*)(b + o_tabdf);
   p->Dsec = Dsec;
   p->sec_nA = (long long)A.size();
   p->sec_ntab = (long long)tab.size();
   return HM_OK;
 }
 
-int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
+template <int AR>
+static cudaError_t sector_launch(Plan* p, const void* x, void* y, long long nvec, cudaStream_t s) {
+  using P = SecAr<AR>;
   const KSector& S = p->ksec;
-  const size_t tabs = sec_tables_bytes(S.N, S.K, p->sec_nA, S.nch, p->sec_ntab);
+  const size_t tabs = sec_tables_bytes(S.N, S.K, p->sec_nA, S.nch, p->sec_ntab, sizeof(typename P::C));
   const int staged = tabs <= kSecTablesMax;
   const size_t smem = (staged ? tabs : 0) + (size_t)2 * S.N * kSecNT;
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_sector<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_sector<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_sector<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long long need = (S.Dsec + kSecNT - 1) / kSecNT;
   const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms() * 8));
-  if (dt == HM_F32)
-    k_sector<float><<<grid, kSecNT, smem, s>>>(S, (const float*)x, (float*)y, (int)nvec, p->sec_nA, p->sec_ntab, staged);
-  else
-    k_sector<double><<<grid, kSecNT, smem, s>>>(S, (const double*)x, (double*)y, (int)nvec, p->sec_nA, p->sec_ntab,
-                                                staged);
-  cudaError_t e = cudaGetLastError();
+  k_sector<AR><<<grid, kSecNT, smem, s>>>(S, (const typename P::TX*)x, (typename P::TY*)y, (int)nvec, p->sec_nA,
+                                          p->sec_ntab, staged);
+  return cudaGetLastError();
+}
+
+int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
+  cudaError_t e;
+  if (dt == HM_F32) {
+    e = sector_launch<AR_F32>(p, x, y, nvec, s);
+  } else {  // FP64: split into float pairs first
+    const float2* xs = nullptr;
+    Scratch xsb;
+    int rc = split_vector(x, p->Dsec * nvec, s, xsb, &xs);
+    if (rc) return rc;
+    e = sector_launch<AR_DF64>(p, xs, y, nvec, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "sector apply launch");
   return HM_OK;
 }

@@ -99,9 +99,10 @@ def test_appendix_d_worked_update_on_gpu():
     x = torch.zeros(6, dtype=torch.float64, device="cuda")
     x[3] = 1.0
     y = h.apply(x).cpu().numpy()
-    want = np.zeros(6)
-    want[5] = J / 2
-    assert np.array_equal(y, want)
+    # the hop lands on packed index 5 alone; its value carries the
+    # double-float coefficient (hi + lo float pair, ~2^-48 relative)
+    assert np.array_equal(np.flatnonzero(y), [5])
+    assert abs(y[5] - J / 2) <= 2.0 ** -45 * (J / 2)
 
 
 def _chain(n, d, jz=1.0, h=0.3, seed=0):
