@@ -228,7 +228,9 @@ int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);
  * touching the GPU, and write the resulting tables as JSON text. which
  * bit 0: H^T instead of H; bit 1: the tile kernel's tables for
  * nvec = which >> 8 (at least 1; HM_ERR_UNSUPPORTED if there is no tile
- * form), else the general kernel's. On success *len = bytes needed including
+ * form); bit 2: the tables of hm_create_sector for digit_total =
+ * which >> 8 (same error codes as hm_create_sector); else the general
+ * kernel's. On success *len = bytes needed including
  * the terminating NUL; the text is written only if buf != NULL and
  * bufsize >= *len. Same error codes as hm_create. */
 int hm_plan_export(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,

@@ -185,19 +185,24 @@ struct KTile {
 // the terms of sites i..j, so the source rank is the target's plus O(j-i+1)
 // table differences: the lookup of Sec. VI without a search.
 // ---------------------------------------------------------------------------
-struct KSecChan {
-  int tab;         // coefficient table base (target digits n_i * dj + n_j)
-  int dj;
-  int16_t si, sj;  // sites (sj = -1: single-site, diagonal)
-  int8_t qi, qj;   // n_target = n_source + q
-  int8_t pad[2];
+struct alignas(16) KSecChan {
+  int tab;         // coefficient table base, entry [n_i * dj + n_j] (target digits)
+  int dtab;        // rank-delta table base for a move on adjacent sites,
+                   // entry [rem_i * rstride + n_i * dj + n_j]; -1: rank update
+                   // from the rank tables
+  int rstride;     // d_i * dj
+  int dj;          // d_j (1 for a single-site channel)
+  int si, sj;      // sites (sj = -1: single-site)
+  int q;           // n_target - n_source on site si (the opposite on sj)
+  int diag;        // q = 0 on both sites
 };
-static_assert(sizeof(KSecChan) == 16, "KSecChan layout");
+static_assert(sizeof(KSecChan) == 32, "KSecChan layout");
 
 struct KSector {
   long long Dsec;          // retained states
   int N, K;                // sites, digit total
   int nch;                 // channels (all conserve the digit sum)
+  int wide;                // rank deltas stored as int64 (else int32)
   const int* d;            // [N] local dimensions capped at K + 1 (rank-table strides)
   const long long* cnt;    // [(N + 1) * (K + 1)] cnt_k[t] at k * (K + 1) + t
   const long long* A;      // rank tables, site k at Aoff[k]: [t * (d_k + 1) + n]
@@ -206,6 +211,7 @@ struct KSector {
   const double* tab_d;     // coefficient pool
   const float* tab_f;
   const float2* tab_df;    // as float pairs (double-float arithmetic)
+  const void* dl;          // rank-delta pool (int32 or int64 entries)
 };
 
 // Launch choice of the apply kernel; 0 = library default for each field.
@@ -257,6 +263,8 @@ struct Plan {
   KSector ksec{};
   void* sec_dev = nullptr;
   long long sec_nA = 0, sec_ntab = 0;   // rank-table and coefficient-pool lengths
+  long long sec_ndl = 0;                // rank-delta pool length
+  bool sec_needA = true;                // some channel updates ranks from the rank tables
 
   // merged channels of H and H^T (H^T empty when H is symmetric) and the
   // identity part, kept for building tile tables per nvec
@@ -287,6 +295,7 @@ void free_plan_device(Plan* p);
 // sector.cu
 int build_sector(Plan* p);   // sector tables from p->chH (after build_plan's host half)
 void free_sector(Plan* p);
+std::string export_sector_json(const Plan* p, long long digit_total, int* rc);
 int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
 // length of the plan's vectors in states: D, or Dsec for a sector plan
 inline long long vec_states(const Plan* p) { return p->sector ? p->Dsec : p->D; }

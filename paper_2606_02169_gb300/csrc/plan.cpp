@@ -783,6 +783,10 @@ int export_plan(Plan* p, int which, std::string& o) {
   HostPlanData hd;
   int rc = derive_plan(p, hd);
   if (rc) return rc;
+  if (which & 4) {  // sector tables for the digit total which >> 8
+    o = export_sector_json(p, which >> 8, &rc);
+    return rc;
+  }
   if (which & 2) {  // tile tables for nvec = which >> 8 (at least 1)
     const bool tr = (which & 1) && !p->hermitian;
     const long long nvec = std::max(1, which >> 8);

@@ -129,3 +129,68 @@ def emulate_tile(T, x):
                 acc[msk] = acc[msk] + fs[w][f[msk]] * gather(k[msk] + fs_off[w][f[msk]])
             y[k] = acc
     return y
+
+
+def emulate_sector(S, x, nvec=1):
+    """The sector kernel's steps on exported sector tables (hm_plan_export
+    bit 2), over all packed rows at once: unranking by the count tables, the
+    coefficient of every channel from the target digits, the source row from
+    the adjacent-site rank-delta table or the rank-table update over sites
+    si..sj, and the diagonal channels summed before they multiply x_F."""
+    Dsec, K = S["Dsec"], S["K"]
+    K1 = K + 1
+    d = S["d"]
+    N = len(d)
+    Aoff = S["Aoff"]
+    cnt = np.asarray(S["cnt"], dtype=np.int64).reshape(N + 1, K1)
+    A = np.asarray(S["A"], dtype=np.int64)
+    dl = np.asarray(S["dl"], dtype=np.int64)
+    tab = np.asarray(S["tab"], dtype=np.float64)
+    F = np.arange(Dsec, dtype=np.int64)
+    r = F.copy()
+    left = np.full(Dsec, K, dtype=np.int64)
+    dig = np.zeros((N, Dsec), dtype=np.int64)
+    rem = np.zeros((N, Dsec), dtype=np.int64)
+    for k in range(N):
+        c = cnt[k + 1]
+        m = np.zeros(Dsec, dtype=np.int64)
+        active = np.ones(Dsec, dtype=bool)
+        while active.any():
+            idx = left - m
+            cm = np.where(idx >= 0, c[np.clip(idx, 0, K)], 0)
+            adv = active & (r >= cm)
+            r[adv] -= cm[adv]
+            m[adv] += 1
+            active = adv
+        dig[k], rem[k] = m, left
+        left = left - m
+
+    def Aat(k, t, n):
+        return A[Aoff[k] + t * (d[k] + 1) + n]
+
+    X = np.asarray(x, dtype=np.float64).reshape(Dsec, nvec)
+    acc = np.zeros((Dsec, nvec))
+    dsum = np.zeros(Dsec)
+    for tb, dtab, rstride, dj, si, sj, qi, qj, diag in S["ch"]:
+        ni = dig[si]
+        nj = dig[sj] if sj >= 0 else np.zeros(Dsec, dtype=np.int64)
+        ci = ni * dj + nj
+        cf = tab[tb + ci]
+        if diag:
+            dsum += cf
+            continue
+        rows = np.flatnonzero(cf != 0)
+        ni, nj, ci = ni[rows], nj[rows], ci[rows]
+        if dtab >= 0:
+            dlt = dl[dtab + rem[si][rows] * rstride + ci]
+        else:
+            q = qi
+            ri = rem[si][rows]
+            dlt = Aat(si, ri, ni - q) - Aat(si, ri, ni)
+            for k in range(si + 1, sj):
+                rk, nk = rem[k][rows], dig[k][rows]
+                dlt = dlt + Aat(k, rk + q, nk) - Aat(k, rk, nk)
+            rj = rem[sj][rows]
+            dlt = dlt + Aat(sj, rj + q, nj - qj) - Aat(sj, rj, nj)
+        acc[rows] += cf[rows, None] * X[rows + dlt]
+    return (acc + dsum[:, None] * X).reshape(-1)
