@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "hm.h"
+#include "sector_types.h"
 
 namespace hm {
 
@@ -172,46 +173,6 @@ struct KTile {
   const int* fs_n;          // [F] leaf slots of each leaf state
   const int* fs_off;        // [fs_w * F] element offsets
   const double* fs_d; const float2* fs_df; const float* fs_f;  // [fs_w * F]
-};
-
-// ---------------------------------------------------------------------------
-// Fixed digit-sum sector (Sec. VI case 2, App. D): retained states are the
-// digit tuples with sum_k n_k = K, packed in ascending full-index order. The
-// packed index of a tuple is its combinatorial rank
-//   rank(n) = sum_k A_k[K - P_k][n_k],   P_k = n_0 + ... + n_{k-1},
-//   A_k[t][n] = sum_{m<n} cnt_{k+1}[t - m],
-// with cnt_k[t] the number of digit tuples of sites k..N-1 summing to t.
-// A hop that changes sites i < j by -q_i, -q_j (q_i + q_j = 0) changes only
-// the terms of sites i..j, so the source rank is the target's plus O(j-i+1)
-// table differences: the lookup of Sec. VI without a search.
-// ---------------------------------------------------------------------------
-struct alignas(16) KSecChan {
-  int tab;         // coefficient table base, entry [n_i * dj + n_j] (target digits)
-  int dtab;        // rank-delta table base for a move on adjacent sites,
-                   // entry [rem_i * rstride + n_i * dj + n_j]; -1: rank update
-                   // from the rank tables
-  int rstride;     // d_i * dj
-  int dj;          // d_j (1 for a single-site channel)
-  int si, sj;      // sites (sj = -1: single-site)
-  int q;           // n_target - n_source on site si (the opposite on sj)
-  int diag;        // q = 0 on both sites
-};
-static_assert(sizeof(KSecChan) == 32, "KSecChan layout");
-
-struct KSector {
-  long long Dsec;          // retained states
-  int N, K;                // sites, digit total
-  int nch;                 // channels (all conserve the digit sum)
-  int wide;                // rank deltas stored as int64 (else int32)
-  const int* d;            // [N] local dimensions capped at K + 1 (rank-table strides)
-  const long long* cnt;    // [(N + 1) * (K + 1)] cnt_k[t] at k * (K + 1) + t
-  const long long* A;      // rank tables, site k at Aoff[k]: [t * (d_k + 1) + n]
-  const int* Aoff;         // [N]
-  const KSecChan* ch;      // [nch]
-  const double* tab_d;     // coefficient pool
-  const float* tab_f;
-  const float2* tab_df;    // as float pairs (double-float arithmetic)
-  const void* dl;          // rank-delta pool (int32 or int64 entries)
 };
 
 // Launch choice of the apply kernel; 0 = library default for each field.
