@@ -15,6 +15,9 @@ Contents
     (Sec. I: Krylov solvers need only y = H x).
   * ``term_gradients``    -- <gy| O_t |x> per term, by applying one-term
     Hamiltonians; ``hellmann_feynman`` -- <psi|O_t|psi>.
+  * ``evolve``            -- y = exp(-i t H) x (Sec. VII: exact propagation
+    under time-dependent or repeatedly rebuilt couplings), the definition
+    written out through a dense eigendecomposition of H (tiny systems).
   * ``sector_*``          -- the globally constrained sector of Sec. VI case 2
     (local digits summing to a fixed total; App. D): enumeration of the
     retained states, combinatorial rank / unrank, the projected apply
@@ -433,3 +436,21 @@ def sector_rows(sites, terms, total, x, rows, nvec=1):
                     if I >= 0:
                         out[o] += c * a * b * x[I]
     return out.reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Time evolution (Sec. VII use case: exact propagation)
+# ----------------------------------------------------------------------------
+
+def evolve(sites, terms, x, t, coefs=None, sector_total=None):
+    """y = exp(-i t H) x (hbar = 1) for a Hermitian term list: H from the
+    Kronecker assembly (restricted to the sector's retained states when
+    sector_total is given), H = V diag(lam) V^H by numpy.linalg.eigh, then
+    y = V diag(exp(-i t lam)) V^H x. Tiny systems only (D <= 8192)."""
+    H = dense(sites, terms, coefs=coefs)
+    if sector_total is not None:
+        b = sector_basis(sites, sector_total)
+        H = H[np.ix_(b, b)]
+    lam, V = np.linalg.eigh(H)
+    x = np.asarray(x, dtype=np.complex128)
+    return V @ (np.exp(-1j * t * lam) * (V.conj().T @ x))
