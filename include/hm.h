@@ -14,7 +14,16 @@
  *   (Sec. II, Sec. IV.B Eq. sourceoffset, App. A).
  *
  * Vectors: caller-owned DEVICE pointers, state-major interleaved: element v
- * of state k is at [k*nvec + v]. Real storage only (HM_F64 / HM_F32).
+ * of state k is at [k*nvec + v]. Real storage (HM_F64 / HM_F32) or complex
+ * storage (HM_C128 / HM_C64: each element an interleaved (re, im) pair, the
+ * layout of C99 double/float _Complex). Every plan holds a real operator (a
+ * term list with an imaginary matrix element is rejected when the plan is
+ * built), so the real and imaginary parts of a complex vector are applied
+ * independently: a complex call with nvec right-hand sides is the real call
+ * with 2*nvec interleaved right-hand sides on the same memory (same kernels,
+ * same results). hm_apply, hm_apply_ex, hm_apply_adjoint,
+ * hm_coupling_gradients_static, hm_batch_apply, hm_tune, hm_tuned_config and
+ * hm_lanczos accept complex dtypes; hm_evolve requires one.
  * Every call is asynchronous on the given CUDA stream (NULL = legacy default
  * stream) unless stated otherwise. Plans are library-owned. Applies of one
  * plan (hm_apply, hm_batch_apply) may run on several streams at once: the
@@ -69,7 +78,7 @@ typedef struct {
     double coef;
 } hm_term;
 
-typedef enum { HM_F64 = 0, HM_F32 = 1 } hm_dtype;
+typedef enum { HM_F64 = 0, HM_F32 = 1, HM_C128 = 2, HM_C64 = 3 } hm_dtype;
 
 /* return codes */
 enum {
@@ -150,7 +159,10 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
  *   gcoef[t]     = sum_v <gy_v| O_t |x_v>        if gcoef != NULL (device,
  *                  nterms doubles, overwritten), O_t = op_i op_j without coef.
  * gy, x: device vectors of dtype. gcoef is always FP64, reduced
- * deterministically (fixed-order two-pass reduction, no atomics). Uses
+ * deterministically (fixed-order two-pass reduction, no atomics). For
+ * complex dtypes gcoef[t] = Re sum_v <gy_v| O_t |x_v> (the real and
+ * imaginary parts as separate real columns), the gradient of a real loss
+ * L(y) with gy = dL/dRe(y) + i dL/dIm(y), coefficients being real. Uses
  * plan-owned scratch of O(nterms * grid) doubles, grown on demand (so the
  * first call of a size should come before any stream capture) and, for
  * HM_F64, per-call pool scratch as in hm_apply for gy and x split once.
@@ -188,10 +200,42 @@ int hm_coupling_gradients_static(hm_handle h, const void* gy, const void* x, dou
  * reorthogonalisation against v_{k-1} and v_k (default off = plain
  * three-term recurrence). Returns HM_LANCZOS_BREAKDOWN (> 0) when beta_k
  * falls below 1e-14 |alpha|max before `steps`. Allocates 3 (4 with psi0)
- * work vectors per call. */
+ * work vectors per call. A complex v0 (HM_C128 / HM_C64) runs the same
+ * recurrence with the Hermitian inner product (alpha and beta stay real). */
 int hm_lanczos(hm_handle h, const void* v0, int32_t steps, hm_dtype dtype, int32_t flags,
                double* alpha, double* beta, int32_t* steps_done, void* psi0_out, double* e0,
                void* stream);
+
+/* Time evolution y = exp(-i t H) x (hbar = 1) of one complex vector (Sec. VII:
+ * exact propagation under time-dependent or repeatedly rebuilt couplings;
+ * Sec. VIII: Krylov methods need only y = H x). Short-iterative Lanczos
+ * propagator (Park and Light, 1986): t is split into nsub equal steps tau;
+ * each builds an m-step Lanczos basis V_m (T_m = V_m^H H V_m tridiagonal,
+ * real) from the current vector u and sets u <- |u| V_m exp(-i tau T_m) e_1,
+ * the small exponential from a Jacobi eigendecomposition on the host.
+ * x, y: device, hm_dim(h) complex values of dtype HM_C128 or HM_C64 (x
+ * read-only, y overwritten, no overlap). 1 <= m <= 128, nsub >= 1, t
+ * finite (negative t runs backwards). flags bit 0: local
+ * reorthogonalisation as in hm_lanczos; bit 1: rebuild the basis in a second
+ * pass of the recurrence instead of storing it (by default the m basis
+ * vectors are stored when they fit in half the free device memory; both ways
+ * give the same y bit for bit). err (host, nullable): sum over the steps of
+ * the a-posteriori estimate beta_m |[ |u| exp(-i tau T_m) e_1 ]_m| of the
+ * Krylov error (Saad 1992). A step whose Krylov space closes (beta_k below
+ * 1e-14 |alpha|max) ends early and exactly. HM_ERR_NOT_HERMITIAN for a
+ * term list that is not self-adjoint; HM_ERR_INVALID_ARG for NaN or Inf in
+ * the recurrence. Allocates 3 work vectors (+1 if nsub > 1, + m if stored).
+ * Synchronous on stream. Works on sector plans (vectors of hm_dim states). */
+int hm_evolve(hm_handle h, const void* x, void* y, double t, int32_t m, int32_t nsub, int32_t flags,
+              hm_dtype dtype, double* err, void* stream);
+
+/* Host only (no GPU): the coefficients hm_evolve combines a Krylov basis
+ * with, c[k] = nu [exp(-i tau T) e_1]_k for k < m as (re, im) pairs in
+ * c[2m], T the real symmetric tridiagonal matrix with diagonal alpha[m] and
+ * off-diagonal beta[m-1] (beta may be NULL for m = 1). 1 <= m <= 128;
+ * non-finite input gives HM_ERR_INVALID_ARG. */
+int hm_krylov_coefficients(const double* alpha, const double* beta, int32_t m, double tau, double nu,
+                           double* c);
 
 /* Batched apply over many plans of uneven size: one persistent launch per
  * 128 instances walks an (instance, block[, chunk]) work list; an instance

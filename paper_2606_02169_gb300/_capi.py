@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhm.so")
 HM_SPIN, HM_BOSON = 0, 1
 OPS = {"I": 0, "Sz": 1, "Sx": 2, "Sy": 3, "Sp": 4, "Sm": 5, "Sz2": 6, "Sp2": 7, "Sm2": 8,
        "N": 9, "a": 10, "adag": 11}
-HM_F64, HM_F32 = 0, 1
+HM_F64, HM_F32, HM_C128, HM_C64 = 0, 1, 2, 3
 
 HM_OK = 0
 HM_ERR_INVALID_ARG = -1
@@ -35,6 +35,7 @@ EXPORTS = [
     "hm_create", "hm_create_sector", "hm_set_coefficients", "hm_dim", "hm_num_terms", "hm_apply", "hm_apply_ex",
     "hm_apply_adjoint", "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune",
     "hm_tuned_config", "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export", "hm_coupling_gradients_static",
+    "hm_evolve", "hm_krylov_coefficients",
 ]
 
 
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
     lib.hm_batch_apply.argtypes = [H, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, ctypes.c_int, vp]
     lib.hm_tune.argtypes = [H, i64, ctypes.c_int, vp]
     lib.hm_tuned_config.argtypes = [H, i64, ctypes.c_int, ctypes.POINTER(i32)]
+    lib.hm_evolve.argtypes = [H, vp, vp, ctypes.c_double, i32, i32, i32, ctypes.c_int, dp, vp]
+    lib.hm_krylov_coefficients.argtypes = [dp, dp, i32, ctypes.c_double, ctypes.c_double, dp]
     lib.hm_destroy.argtypes = [H]
     lib.hm_plan_export.argtypes = [ctypes.POINTER(hm_site), i32, ctypes.POINTER(hm_term), i32, i32,
                                    ctypes.c_char_p, i64, ctypes.POINTER(i64)]
@@ -99,10 +102,24 @@ def load(path: str = LIB_PATH):
     lib.hm_last_error.restype = ctypes.c_char_p
     for name in ("hm_create", "hm_create_sector", "hm_set_coefficients", "hm_apply", "hm_apply_ex", "hm_apply_adjoint",
                  "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune", "hm_tuned_config",
-                 "hm_destroy"):
+                 "hm_destroy", "hm_evolve", "hm_krylov_coefficients"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def krylov_coefficients(alpha, beta, tau, nu=1.0):
+    """Host-only: c = nu exp(-i tau T) e_1 for T = tridiag(beta, alpha, beta)
+    (the combination hm_evolve applies to its Krylov basis), complex array."""
+    import numpy as np
+    lib = load()
+    m = len(alpha)
+    a = (ctypes.c_double * m)(*[float(v) for v in alpha])
+    b = (ctypes.c_double * max(1, m - 1))(*[float(v) for v in beta[: m - 1]])
+    c = (ctypes.c_double * (2 * m))()
+    check(lib.hm_krylov_coefficients(a, b if m > 1 else None, m, float(tau), float(nu), c), "hm_krylov_coefficients")
+    v = np.frombuffer(c, dtype=np.float64).copy()
+    return v[0::2] + 1j * v[1::2]
 
 
 def plan_export(sites, terms, which=0):

@@ -27,7 +27,19 @@ static Plan* as_plan(hm_handle h) {
 }
 
 
+constexpr int kKrylovMax = 128;  // Krylov dimension limit of hm_evolve
+
 static size_t esize(hm_dtype dt) { return dt == HM_F32 ? 4 : 8; }
+
+// Complex storage: every plan holds a real operator (an imaginary matrix
+// element is rejected when the plan is built), so the real and imaginary
+// parts of a complex vector are applied independently -- nvec complex
+// right-hand sides are 2 * nvec interleaved real ones on the same memory.
+static void real_view(hm_dtype& dt, long long& nvec) {
+  if (dt != HM_C128 && dt != HM_C64) return;
+  dt = dt == HM_C128 ? HM_F64 : HM_F32;
+  if (nvec > 0 && nvec < (1LL << 40)) nvec *= 2;
+}
 
 static bool overlap(const void* a, const void* b, size_t bytes) {
   auto pa = (uintptr_t)a, pb = (uintptr_t)b;
@@ -171,17 +183,21 @@ int32_t hm_num_terms(hm_handle h) {
   return (int32_t)p->terms.size();
 }
 
-int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream) {
+int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
+  long long nvec = nvec_in;
+  real_view(dtype, nvec);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
   if (p->sector) return launch_sector(p, x, y, nvec, dtype, (cudaStream_t)stream);
   return launch_apply(p, x, y, nvec, dtype, (cudaStream_t)stream, tuned_cfg(p, dtype, nvec));
 }
 
-int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
+int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream) {
   Plan* p = as_plan(h);
+  long long nvec = nvec_in;
+  real_view(dtype, nvec);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
   if ((rc = no_sector(p, "hm_apply_ex"))) return rc;
@@ -209,8 +225,10 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
 }
 
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
-                     int64_t nvec, hm_dtype dtype, void* stream) {
+                     int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
+  long long nvec = nvec_in;
+  real_view(dtype, nvec);
   if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
   if (int rc = no_sector(p, "hm_apply_adjoint")) return rc;
   if (!gx && !gcoef) return HM_OK;
@@ -235,13 +253,15 @@ int hm_lanczos(hm_handle h, const void* v0, int32_t steps, hm_dtype dtype, int32
     set_error("invalid Lanczos arguments");
     return HM_ERR_INVALID_ARG;
   }
+  long long nvec = 1;
+  real_view(dtype, nvec);
   if (dtype != HM_F64 && dtype != HM_F32) { set_error("bad dtype"); return HM_ERR_INVALID_ARG; }
   if (!p->hermitian) {
     set_error("Lanczos needs a self-adjoint term list");
     return HM_ERR_NOT_HERMITIAN;
   }
   int sd = 0;
-  int rc = run_lanczos(p, v0, steps, dtype, flags, alpha, beta, &sd, psi0_out, e0, (cudaStream_t)stream);
+  int rc = run_lanczos(p, v0, steps, dtype, nvec, flags, alpha, beta, &sd, psi0_out, e0, (cudaStream_t)stream);
   *steps_done = sd;
   return rc;
 }
@@ -269,9 +289,11 @@ int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out) {
   return HM_OK;
 }
 
-int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int64_t nvec,
+int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int64_t nvec_in,
                    hm_dtype dtype, void* stream) {
   Plan* b = as_plan(batch);
+  long long nvec = nvec_in;
+  real_view(dtype, nvec);
   if (!b || !b->is_batch || !xs || !ys || nvec < 1) {
     set_error("invalid batch apply arguments");
     return HM_ERR_INVALID_ARG;
@@ -309,8 +331,10 @@ int hm_destroy(hm_handle h) {
 // per (dtype, nvec), also in a process-wide cache keyed by the site
 // dimensions and channel counts. Each candidate: one untimed launch, then the
 // minimum of three event-timed launches.
-int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
+int hm_tune(hm_handle h, int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
+  long long nvec = nvec_in;
+  real_view(dtype, nvec);
   if (!p || p->is_batch || nvec < 1 || (dtype != HM_F64 && dtype != HM_F32)) {
     set_error("invalid tune arguments");
     return HM_ERR_INVALID_ARG;
@@ -399,8 +423,10 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream) {
 }
 
 /* Launch choice hm_tune stored for (nvec, dtype); see include/hm.h. */
-int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out) {
+int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) {
   Plan* p = as_plan(h);
+  long long nvec = nvec_in;
+  real_view(dtype, nvec);
   if (!p || p->is_batch || !out) {
     set_error("invalid arguments");
     return HM_ERR_INVALID_ARG;
@@ -410,6 +436,45 @@ int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out) {
   out[1] = c.s;
   out[2] = c.mb;
   out[3] = c.kern;
+  return HM_OK;
+}
+
+/* Time evolution y = exp(-i t H) x; see include/hm.h. */
+int hm_evolve(hm_handle h, const void* x, void* y, double t, int32_t m, int32_t nsub, int32_t flags,
+              hm_dtype dtype, double* err, void* stream) {
+  Plan* p = as_plan(h);
+  if (dtype != HM_C128 && dtype != HM_C64) {
+    set_error("hm_evolve needs complex storage (HM_C128 or HM_C64)");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (m < 1 || m > kKrylovMax || nsub < 1 || !std::isfinite(t) || (flags & ~3)) {
+    set_error("hm_evolve needs 1 <= m <= 128, nsub >= 1, a finite t and flags in bits 0..1");
+    return HM_ERR_INVALID_ARG;
+  }
+  long long nvec = 1;
+  real_view(dtype, nvec);
+  int rc = check_vec_args(p, x, y, nvec, dtype);
+  if (rc) return rc;
+  if (!p->hermitian) {
+    set_error("time evolution needs a self-adjoint term list");
+    return HM_ERR_NOT_HERMITIAN;
+  }
+  return run_evolve(p, x, y, t, m, nsub, flags, dtype, err, (cudaStream_t)stream);
+}
+
+/* Host-only Krylov propagator coefficients; see include/hm.h. */
+int hm_krylov_coefficients(const double* alpha, const double* beta, int32_t m, double tau, double nu, double* c) {
+  if (!alpha || !c || m < 1 || m > kKrylovMax || (m > 1 && !beta) || !std::isfinite(tau) || !std::isfinite(nu)) {
+    set_error("invalid Krylov coefficient arguments");
+    return HM_ERR_INVALID_ARG;
+  }
+  std::vector<double> a(alpha, alpha + m), b;
+  if (m > 1) b.assign(beta, beta + m - 1);
+  for (double v : a) if (!std::isfinite(v)) { set_error("non-finite alpha"); return HM_ERR_INVALID_ARG; }
+  for (double v : b) if (!std::isfinite(v)) { set_error("non-finite beta"); return HM_ERR_INVALID_ARG; }
+  std::vector<double> cc;
+  krylov_coeffs(a, b, tau, nu, cc);
+  std::copy(cc.begin(), cc.end(), c);
   return HM_OK;
 }
 

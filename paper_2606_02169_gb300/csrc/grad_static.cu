@@ -53,6 +53,10 @@ static int static_partials(double** out) {
 extern "C" int hm_coupling_gradients_static(hm_handle h, const void* gy, const void* x, double* gcoef,
                                             int64_t nvec, hm_dtype dtype, void* stream) {
   using namespace hm;
+  if (dtype == HM_C128 || dtype == HM_C64) {  // real H: the (re, im) parts are 2 * nvec real columns
+    dtype = dtype == HM_C128 ? HM_F64 : HM_F32;
+    if (nvec > 0 && nvec < (1LL << 40)) nvec *= 2;
+  }
   Plan* p = reinterpret_cast<Plan*>(h);
   if (!p || p->magic != 0x484d504cU || p->is_batch) {
     set_error("invalid handle");

@@ -301,8 +301,16 @@ void scratch_trim();
 int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
-int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,
+// Lanczos on vectors of vec_states * nvec elements of the real dtype dt
+// (nvec = 2 for a complex vector of a real H)
+int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, long long nvec, int flags, double* alpha,
                 double* beta, int* steps_done, void* psi0, double* e0, cudaStream_t s);
+// y = exp(-i t H) x for one complex vector stored as interleaved pairs of dt
+int run_evolve(Plan* p, const void* x, void* y, double t, int m, int nsub, int flags, hm_dtype dt, double* err,
+               cudaStream_t s);
+// c[k] = nu [exp(-i tau T) e_1]_k, (re, im) pairs, T = tridiag(b, a, b)
+void krylov_coeffs(const std::vector<double>& a, const std::vector<double>& b, double tau, double nu,
+                   std::vector<double>& c);
 int batch_setup(Plan* b);
 int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec, hm_dtype dt,
                  cudaStream_t s);

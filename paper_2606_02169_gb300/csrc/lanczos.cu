@@ -1,4 +1,5 @@
-// Device Lanczos ground state (Sec. I: Krylov solvers consume only y = H x).
+// Device Lanczos ground state and time evolution (Sec. I, Sec. VIII: Krylov
+// methods consume only y = H x; Sec. VII: exact propagation).
 //   w = H v_k;  alpha_k = <v_k, w>;  w -= alpha_k v_k + beta_{k-1} v_{k-1};
 //   [optional second Gram-Schmidt pass against v_k, v_{k-1}];
 //   beta_k = ||w||;  v_{k+1} = w / beta_k.
@@ -10,6 +11,10 @@
 // host round trip. The tridiagonal eigenproblem is solved on the host in
 // FP64 (Sturm-sequence bisection for the lowest eigenvalue, then inverse
 // iteration with a partially pivoted tridiagonal solve for its vector).
+// Time evolution y = exp(-i t H) x is the short-iterative Lanczos propagator
+// (Park and Light, 1986): per step tau, u <- |u| V_m exp(-i tau T_m) e_1,
+// with exp(-i tau T_m) from a Jacobi eigendecomposition of T_m on the host
+// and the Krylov basis V_m stored on the device or rebuilt by a second pass.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -288,44 +293,76 @@ static std::vector<double> lowest_eigvec(const std::vector<double>& a, const std
 }
 
 // ---------------------------------------------------------------------------
-// driver
+// the recurrence
 // ---------------------------------------------------------------------------
-template <class T>
-static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, double* alpha,
-                     double* beta, int* steps_done, T* psi0, double* e0, cudaStream_t s) {
-  const long long n = vec_states(p);
-  const int vb = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
-  const int rb = (int)std::min<long long>((n + kRedThreads - 1) / kRedThreads, kRedBlocks);
-  T *V = nullptr;
-  double* dsc = nullptr;  // [2 rb partials][alpha steps][beta steps][tmp 4]
-  cudaError_t e = cudaMalloc(&V, sizeof(T) * n * 3);
-  if (e != cudaSuccess) return cuda_fail(e, "Lanczos work vectors");
-  e = cudaMalloc(&dsc, sizeof(double) * (2 * (size_t)rb + 2 * (size_t)steps + 8));
-  if (e != cudaSuccess) {
-    cudaFree(V);
-    return cuda_fail(e, "Lanczos scalars");
-  }
-  T* vk = V;
-  T* vp = V + n;
-  T* w = V + 2 * n;
-  double* part = dsc;
-  double* dal = dsc + 2 * rb;
-  double* dbe = dal + steps;
-  double* tmp = dbe + steps;
-  int rc = HM_OK;
 
-  auto dot = [&](const T* a, const T* b, double* out, int sq) {
+// Work vectors, device scalars and launch shapes of one Lanczos recurrence on
+// vectors of n = states * nvec elements (nvec = 2: the real and imaginary
+// parts of a complex vector, interleaved; for a real H the recurrence on the
+// pairs is the complex recurrence, whose alpha and beta are real).
+template <class T>
+struct Recurrence {
+  Plan* p = nullptr;
+  hm_dtype dt = HM_F64;
+  long long nvec = 1, n = 0;
+  int flags = 0, vb = 1, rb = 1;
+  cudaStream_t s = nullptr;
+  T* V = nullptr;
+  T *vk = nullptr, *vp = nullptr, *w = nullptr;
+  double* dsc = nullptr;  // [2 rb partials][alpha steps][beta steps][tmp 8]
+  double *part = nullptr, *dal = nullptr, *dbe = nullptr, *tmp = nullptr;
+
+  int init(Plan* p_, hm_dtype dt_, long long nvec_, int flags_, int steps, cudaStream_t s_) {
+    p = p_;
+    dt = dt_;
+    nvec = nvec_;
+    flags = flags_;
+    s = s_;
+    n = vec_states(p) * nvec;
+    vb = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+    rb = (int)std::min<long long>((n + kRedThreads - 1) / kRedThreads, kRedBlocks);
+    cudaError_t e = cudaMalloc(&V, sizeof(T) * n * 3);
+    if (e != cudaSuccess) {
+      V = nullptr;
+      return cuda_fail(e, "Lanczos work vectors");
+    }
+    e = cudaMalloc(&dsc, sizeof(double) * (2 * (size_t)rb + 2 * (size_t)steps + 8));
+    if (e != cudaSuccess) {
+      dsc = nullptr;
+      return cuda_fail(e, "Lanczos scalars");
+    }
+    vk = V;
+    vp = V + n;
+    w = V + 2 * n;
+    part = dsc;
+    dal = dsc + 2 * rb;
+    dbe = dal + steps;
+    tmp = dbe + steps;
+    return HM_OK;
+  }
+  ~Recurrence() {
+    if (s || V || dsc) cudaStreamSynchronize(s);
+    if (V) cudaFree(V);
+    if (dsc) cudaFree(dsc);
+  }
+
+  void dot(const T* a, const T* b, double* out, int sq) {
     k_dot<T><<<rb, kRedThreads, 0, s>>>(a, b, n, part);
     k_finish<<<1, 256, 0, s>>>(part, rb, out, sq);
-  };
-  // one pass of the recurrence; if psi != nullptr, also psi += u[k] v_k
-  auto run = [&](int m, const std::vector<double>* u, T* psi) -> int {
+  }
+
+  // One pass of m steps from v0 (tmp[0] = |v0|, v_0 = v0 / |v0|);
+  // at_step(k, v_k) is queued before the apply of step k. beta of the last
+  // step is formed too when last_beta (the residual norm of the m-step space).
+  template <class F>
+  int run(const T* v0, int m, bool last_beta, F&& at_step) {
     dot(v0, v0, tmp, 1);
     k_scale<T><<<vb, 256, 0, s>>>(vk, v0, tmp, 0.0, n);
     cudaMemsetAsync(vp, 0, sizeof(T) * n, s);
     for (int k = 0; k < m; ++k) {
-      if (psi) k_axpy<T><<<vb, 256, 0, s>>>(psi, vk, (*u)[k], n);
-      int arc = apply_on(p, false, vk, w, 1, dt, s, tuned_cfg(p, dt, 1), false);
+      int arc = at_step(k, (const T*)vk);
+      if (arc) return arc;
+      arc = apply_on(p, false, vk, w, nvec, dt, s, tuned_cfg(p, dt, nvec), false);
       if (arc) return arc;
       dot(vk, w, dal + k, 0);
       const T* vpk = k > 0 ? vp : nullptr;
@@ -341,73 +378,271 @@ static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, int flags, do
       } else {
         k_axpy2_dot<T><<<rb, kRedThreads, 0, s>>>(w, vk, vpk, dal + k, k > 0 ? dbe + k - 1 : nullptr, n, 1, part);
       }
-      if (last) break;
+      if (last && !last_beta) break;
       k_finish<<<1, 256, 0, s>>>(part, rb, dbe + k, 1);
-      std::swap(vp, vk);                         // v_{k-1} <- v_k
+      if (last) break;
+      std::swap(vp, vk);                                      // v_{k-1} <- v_k
       k_scale<T><<<vb, 256, 0, s>>>(vk, w, dbe + k, 0.0, n);  // v_{k+1} = w / beta_k
     }
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return cuda_fail(le, "Lanczos kernels");
     return HM_OK;
-  };
-
-  rc = run(steps, nullptr, nullptr);
-  if (rc == HM_OK) {
-    std::vector<double> ha(steps), hb(steps, 0.0);
-    e = cudaMemcpyAsync(ha.data(), dal, sizeof(double) * steps, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && steps > 1)
-      e = cudaMemcpyAsync(hb.data(), dbe, sizeof(double) * (steps - 1), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) rc = cuda_fail(e, "Lanczos scalars to host");
-    if (rc == HM_OK) {
-      double amax = 0.0;
-      for (double v : ha) amax = std::max(amax, std::fabs(v));
-      int m = steps;
-      for (int k = 0; k + 1 < steps; ++k)
-        if (!(hb[k] > 1e-14 * std::max(1.0, amax))) {  // breakdown (also catches NaN)
-          m = k + 1;
-          rc = HM_LANCZOS_BREAKDOWN;
-          break;
-        }
-      std::vector<double> a(ha.begin(), ha.begin() + m), b(hb.begin(), hb.begin() + std::max(0, m - 1));
-      for (int k = 0; k < steps; ++k) {
-        alpha[k] = k < m ? ha[k] : 0.0;
-        beta[k] = k + 1 < m ? hb[k] : 0.0;
-      }
-      *steps_done = m;
-      *e0 = lowest_eigenvalue(a, b);
-      if (psi0) {
-        std::vector<double> u = lowest_eigvec(a, b, *e0);
-        cudaMemsetAsync(psi0, 0, sizeof(T) * n, s);
-        int rc2 = run(m, &u, psi0);
-        if (rc2 != HM_OK) rc = rc2;
-        else {
-          dot(psi0, psi0, tmp + 3, 1);
-          double nrm = 0.0;
-          e = cudaMemcpyAsync(&nrm, tmp + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-          if (e == cudaSuccess && nrm > 0.0) {
-            k_copy_scaled<T><<<vb, 256, 0, s>>>(psi0, psi0, 1.0 / nrm, n);
-            e = cudaStreamSynchronize(s);
-          }
-          if (e != cudaSuccess) rc = cuda_fail(e, "Ritz vector");
-        }
-      }
-    }
   }
-  cudaStreamSynchronize(s);
-  cudaFree(V);
-  cudaFree(dsc);
+
+  // alpha[0..m), beta[0..nb) and |v0| to the host
+  int scalars(int m, int nb, std::vector<double>& ha, std::vector<double>& hb, double* nu) {
+    ha.assign(m, 0.0);
+    hb.assign(std::max(nb, 0), 0.0);
+    cudaError_t e = cudaMemcpyAsync(ha.data(), dal, sizeof(double) * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nb > 0)
+      e = cudaMemcpyAsync(hb.data(), dbe, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nu) e = cudaMemcpyAsync(nu, tmp, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "Lanczos scalars to host");
+    return HM_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// ground state
+// ---------------------------------------------------------------------------
+template <class T>
+static int lanczos_t(Plan* p, const T* v0, int steps, hm_dtype dt, long long nvec, int flags, double* alpha,
+                     double* beta, int* steps_done, T* psi0, double* e0, cudaStream_t s) {
+  Recurrence<T> R;
+  int rc = R.init(p, dt, nvec, flags, steps, s);
+  if (rc) return rc;
+  const long long n = R.n;
+  auto none = [](int, const T*) -> int { return HM_OK; };
+  rc = R.run(v0, steps, false, none);
+  if (rc) return rc;
+  std::vector<double> ha, hb;
+  rc = R.scalars(steps, steps - 1, ha, hb, nullptr);
+  if (rc) return rc;
+  hb.push_back(0.0);
+  double amax = 0.0;
+  for (double v : ha) amax = std::max(amax, std::fabs(v));
+  int m = steps;
+  for (int k = 0; k + 1 < steps; ++k)
+    if (!(hb[k] > 1e-14 * std::max(1.0, amax))) {  // breakdown (also catches NaN)
+      m = k + 1;
+      rc = HM_LANCZOS_BREAKDOWN;
+      break;
+    }
+  std::vector<double> a(ha.begin(), ha.begin() + m), b(hb.begin(), hb.begin() + std::max(0, m - 1));
+  for (int k = 0; k < steps; ++k) {
+    alpha[k] = k < m ? ha[k] : 0.0;
+    beta[k] = k + 1 < m ? hb[k] : 0.0;
+  }
+  *steps_done = m;
+  *e0 = lowest_eigenvalue(a, b);
+  if (psi0) {
+    // the Ritz vector, assembled in a second pass of the same recurrence
+    std::vector<double> u = lowest_eigvec(a, b, *e0);
+    cudaMemsetAsync(psi0, 0, sizeof(T) * n, s);
+    int rc2 = R.run(v0, m, false, [&](int k, const T* vk) -> int {
+      k_axpy<T><<<R.vb, 256, 0, s>>>(psi0, vk, u[k], n);
+      return HM_OK;
+    });
+    if (rc2 != HM_OK) return rc2;
+    R.dot(psi0, psi0, R.tmp + 3, 1);
+    double nrm = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&nrm, R.tmp + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && nrm > 0.0) {
+      k_copy_scaled<T><<<R.vb, 256, 0, s>>>(psi0, psi0, 1.0 / nrm, n);
+      e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "Ritz vector");
+  }
   return rc;
 }
 
-int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, int flags, double* alpha,
+int run_lanczos(Plan* p, const void* v0, int steps, hm_dtype dt, long long nvec, int flags, double* alpha,
                 double* beta, int* steps_done, void* psi0, double* e0, cudaStream_t s) {
   if (dt == HM_F32)
-    return lanczos_t<float>(p, (const float*)v0, steps, dt, flags, alpha, beta, steps_done,
-                            (float*)psi0, e0, s);
-  return lanczos_t<double>(p, (const double*)v0, steps, dt, flags, alpha, beta, steps_done,
+    return lanczos_t<float>(p, (const float*)v0, steps, dt, nvec, flags, alpha, beta, steps_done, (float*)psi0,
+                            e0, s);
+  return lanczos_t<double>(p, (const double*)v0, steps, dt, nvec, flags, alpha, beta, steps_done,
                            (double*)psi0, e0, s);
+}
+
+// ---------------------------------------------------------------------------
+// time evolution
+// ---------------------------------------------------------------------------
+
+// y += (cr + i ci) v on interleaved (re, im) pairs
+template <class T>
+__global__ void k_caxpy(T* __restrict__ y, const T* __restrict__ v, double cr, double ci, long long npairs) {
+  const float2 pr = pair_of(cr), pi = pair_of(ci), mpi = pair_of(-ci);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T vr = v[2 * i], vi = v[2 * i + 1];
+    if constexpr (sizeof(T) == 4) {
+      y[2 * i] = lin3(y[2 * i], pr, vr, mpi, vi);
+      y[2 * i + 1] = lin3(y[2 * i + 1], pr, vi, pi, vr);
+    } else {
+      y[2 * i] = fma(cr, vr, fma(-ci, vi, y[2 * i]));
+      y[2 * i + 1] = fma(cr, vi, fma(ci, vr, y[2 * i + 1]));
+    }
+  }
+}
+
+// Eigendecomposition of the real symmetric tridiagonal T (diagonal a,
+// off-diagonal b) by the cyclic Jacobi method: rotations in the (p, q)
+// plane with tan t the smaller root of t^2 + 2 t theta - 1 = 0, theta =
+// (T_qq - T_pp) / (2 T_pq), until the off-diagonal mass is negligible.
+// lam[j] and column j of Q (row-major, Q[k * m + j]) are the eigenpairs.
+static void jacobi_eig(const std::vector<double>& a, const std::vector<double>& b, std::vector<double>& lam,
+                       std::vector<double>& Q) {
+  const int m = (int)a.size();
+  std::vector<double> A((size_t)m * m, 0.0);
+  Q.assign((size_t)m * m, 0.0);
+  double fro = 0.0;
+  for (int i = 0; i < m; ++i) {
+    A[(size_t)i * m + i] = a[i];
+    Q[(size_t)i * m + i] = 1.0;
+    fro += a[i] * a[i];
+    if (i + 1 < m) {
+      A[(size_t)i * m + i + 1] = A[(size_t)(i + 1) * m + i] = b[i];
+      fro += 2 * b[i] * b[i];
+    }
+  }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += A[(size_t)p * m + q] * A[(size_t)p * m + q];
+    if (off <= 1e-34 * fro || off == 0.0) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[(size_t)p * m + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+          A[(size_t)k * m + p] = c * akp - sn * akq;
+          A[(size_t)k * m + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+          A[(size_t)p * m + k] = c * apk - sn * aqk;
+          A[(size_t)q * m + k] = sn * apk + c * aqk;
+        }
+        A[(size_t)p * m + q] = A[(size_t)q * m + p] = 0.0;
+        for (int k = 0; k < m; ++k) {
+          const double qkp = Q[(size_t)k * m + p], qkq = Q[(size_t)k * m + q];
+          Q[(size_t)k * m + p] = c * qkp - sn * qkq;
+          Q[(size_t)k * m + q] = sn * qkp + c * qkq;
+        }
+      }
+  }
+  lam.resize(m);
+  for (int i = 0; i < m; ++i) lam[i] = A[(size_t)i * m + i];
+}
+
+// c[k] = nu [exp(-i tau T) e_1]_k as (re, im) pairs, T = tridiag(b, a, b)
+void krylov_coeffs(const std::vector<double>& a, const std::vector<double>& b, double tau, double nu,
+                   std::vector<double>& c) {
+  const int m = (int)a.size();
+  std::vector<double> lam, Q;
+  jacobi_eig(a, b, lam, Q);
+  c.assign(2 * (size_t)m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    const double fr = std::cos(tau * lam[j]) * Q[j], fi = -std::sin(tau * lam[j]) * Q[j];  // Q[0 * m + j]
+    for (int k = 0; k < m; ++k) {
+      c[2 * k] += nu * Q[(size_t)k * m + j] * fr;
+      c[2 * k + 1] += nu * Q[(size_t)k * m + j] * fi;
+    }
+  }
+}
+
+template <class T>
+static int evolve_t(Plan* p, const T* x, T* y, double t, int m, int nsub, int flags, hm_dtype dt, double* err,
+                    cudaStream_t s) {
+  Recurrence<T> R;
+  int rc = R.init(p, dt, 2, flags, m, s);
+  if (rc) return rc;
+  const long long n = R.n;
+  T* B = nullptr;  // the Krylov basis, when stored
+  T* scratch = nullptr;
+  if (!(flags & 2)) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (size_t)m * n * sizeof(T) <= fr / 2 &&
+        cudaMalloc(&B, (size_t)m * n * sizeof(T)) != cudaSuccess) {
+      B = nullptr;
+      cudaGetLastError();  // fall back to the second pass
+    }
+  }
+  if (nsub > 1) {
+    cudaError_t e = cudaMalloc(&scratch, (size_t)n * sizeof(T));
+    if (e != cudaSuccess) {
+      if (B) cudaFree(B);
+      return cuda_fail(e, "evolution scratch vector");
+    }
+  }
+  const double tau = t / nsub;
+  double esum = 0.0;
+  const T* u = x;
+  for (int j = 0; j < nsub && rc == HM_OK; ++j) {
+    T* out = ((nsub - 1 - j) % 2 == 0) ? y : scratch;
+    rc = R.run(u, m, true, [&](int k, const T* vk) -> int {
+      if (!B) return HM_OK;
+      cudaError_t e = cudaMemcpyAsync(B + (size_t)k * n, vk, sizeof(T) * n, cudaMemcpyDeviceToDevice, s);
+      return e == cudaSuccess ? HM_OK : cuda_fail(e, "Krylov basis copy");
+    });
+    if (rc) break;
+    std::vector<double> ha, hb;
+    double nu = 0.0;
+    rc = R.scalars(m, m, ha, hb, &nu);
+    if (rc) break;
+    double amax = 0.0;
+    for (double v : ha)
+      if (std::isfinite(v)) amax = std::max(amax, std::fabs(v));
+    int me = m;
+    for (int k = 0; k + 1 < m; ++k)
+      if (!(hb[k] > 1e-14 * std::max(1.0, amax))) {  // invariant Krylov space: exact
+        me = k + 1;
+        break;
+      }
+    bool finite = std::isfinite(nu) && (me < m || std::isfinite(hb[m - 1]));
+    for (int k = 0; k < me; ++k) finite = finite && std::isfinite(ha[k]);
+    if (!finite) {
+      set_error("non-finite value in the Krylov recurrence (x or H holds NaN or Inf)");
+      rc = HM_ERR_INVALID_ARG;
+      break;
+    }
+    std::vector<double> a(ha.begin(), ha.begin() + me), b(hb.begin(), hb.begin() + (me - 1)), c;
+    krylov_coeffs(a, b, tau, nu, c);
+    if (me == m) esum += hb[m - 1] * std::hypot(c[2 * (m - 1)], c[2 * (m - 1) + 1]);
+    cudaMemsetAsync(out, 0, sizeof(T) * n, s);
+    if (B) {
+      for (int k = 0; k < me; ++k)
+        k_caxpy<T><<<R.vb, 256, 0, s>>>(out, B + (size_t)k * n, c[2 * k], c[2 * k + 1], n / 2);
+    } else {  // second pass of the same recurrence: the same v_k, bit for bit
+      rc = R.run(u, me, false, [&](int k, const T* vk) -> int {
+        k_caxpy<T><<<R.vb, 256, 0, s>>>(out, vk, c[2 * k], c[2 * k + 1], n / 2);
+        return HM_OK;
+      });
+    }
+    cudaError_t le = cudaGetLastError();
+    if (rc == HM_OK && le != cudaSuccess) rc = cuda_fail(le, "evolution kernels");
+    u = out;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (rc == HM_OK && e != cudaSuccess) rc = cuda_fail(e, "evolution");
+  if (B) cudaFree(B);
+  if (scratch) cudaFree(scratch);
+  if (err) *err = esum;
+  return rc;
+}
+
+int run_evolve(Plan* p, const void* x, void* y, double t, int m, int nsub, int flags, hm_dtype dt, double* err,
+               cudaStream_t s) {
+  if (dt == HM_F32)
+    return evolve_t<float>(p, (const float*)x, (float*)y, t, m, nsub, flags, dt, err, s);
+  return evolve_t<double>(p, (const double*)x, (double*)y, t, m, nsub, flags, dt, err, s);
 }
 
 }  // namespace hm

@@ -15,12 +15,16 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dtype_code(t: torch.Tensor) -> int:
-    if t.dtype == torch.float64:
-        return C.HM_F64
-    if t.dtype == torch.float32:
-        return C.HM_F32
-    raise TypeError(f"vectors must be float64 or float32, got {t.dtype}")
+_CODES = {torch.float64: C.HM_F64, torch.float32: C.HM_F32, torch.complex128: C.HM_C128,
+          torch.complex64: C.HM_C64}
+
+
+def _dtype_code(t) -> int:
+    """Library dtype of a tensor (or of a torch dtype)."""
+    dt = t if isinstance(t, torch.dtype) else t.dtype
+    if dt not in _CODES:
+        raise TypeError(f"vectors must be float64, float32, complex128 or complex64, got {dt}")
+    return _CODES[dt]
 
 
 def _check_vec(t: torch.Tensor, name: str):
@@ -162,16 +166,32 @@ class Hamiltonian:
         return {"e0": e0.value, "alpha": list(a)[:m], "beta": list(b)[: max(0, m - 1)], "steps": m,
                 "psi0": psi, "breakdown": rc == C.HM_LANCZOS_BREAKDOWN}
 
+    def evolve(self, x: torch.Tensor, t: float, m: int = 30, substeps: int = 1, reorth: bool = False,
+               recompute: bool = False, out: torch.Tensor | None = None, stream=None):
+        """y = exp(-i t H) x for a complex128/complex64 vector of D elements
+        (short-iterative Lanczos, m Krylov vectors per substep). Returns
+        (y, error estimate)."""
+        _check_vec(x, "x")
+        if not x.is_complex() or x.numel() != self.D:
+            raise ValueError("x must be a complex vector of D elements")
+        y = torch.empty_like(x) if out is None else out
+        _check_vec(y, "out")
+        err = ctypes.c_double(0.0)
+        flags = (1 if reorth else 0) | (2 if recompute else 0)
+        C.check(self._lib.hm_evolve(self._h, x.data_ptr(), y.data_ptr(), float(t), int(m), int(substeps), flags,
+                                    _dtype_code(x), ctypes.byref(err), _stream(stream)), "hm_evolve")
+        return y, err.value
+
     def tune(self, nvec: int = 1, dtype=torch.float64, stream=None):
         """Autotune the apply launch for (nvec, dtype); returns the stored choice."""
-        code = C.HM_F64 if dtype == torch.float64 else C.HM_F32
+        code = _dtype_code(dtype)
         C.check(self._lib.hm_tune(self._h, int(nvec), code, _stream(stream)), "hm_tune")
         return self.tuned_config(nvec, dtype)
 
     def tuned_config(self, nvec: int = 1, dtype=torch.float64):
         """dict(ctas, s, mb, kernel) of the stored launch choice (0 = library
         default; kernel 1 = general, 2 = tile)."""
-        code = C.HM_F64 if dtype == torch.float64 else C.HM_F32
+        code = _dtype_code(dtype)
         out = (ctypes.c_int32 * 4)()
         C.check(self._lib.hm_tuned_config(self._h, int(nvec), code, out), "hm_tuned_config")
         return {"ctas": out[0], "s": out[1], "mb": out[2], "kernel": out[3]}
