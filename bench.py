@@ -614,6 +614,38 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     out["adjoint_4x5_f64"] = {"ms_forward": ms_fwd, "ms_adjoint_gx_and_gcoef": ms_adj,
                               "ms_gcoef_only": ms_grad, "adjoint_over_forward": ms_adj / ms_fwd,
                               "nterms": hl.nterms}
+    del hl, xl, gl, yl, gx, gc
+    torch.cuda.empty_cache()
+
+    # time evolution exp(-i t H) x of a complex128 vector on the headline
+    # workload: one short-iterative Lanczos step of m = 30 Krylov vectors
+    # (basis stored, and rebuilt by a second pass), beside the complex apply
+    xc = torch.complex(x, W.torch_vector(D, 23, dtype=torch.float64))
+    xc = xc / torch.linalg.vector_norm(xc)
+    yc = torch.empty_like(xc)
+    if args.tune:
+        h.tune(1, torch.complex128)
+    k = 10
+    ms_capply = timed(lambda: h.apply(xc, out=yc), k, 3, 1, stream) / k
+    mk, te = 30, 0.5
+
+    def evolve_ms(recompute):
+        h.evolve(xc, te, m=mk, out=yc, recompute=recompute)     # warm-up (allocations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, est = h.evolve(xc, te, m=mk, out=yc, recompute=recompute)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3, est
+
+    ms_ev, est = evolve_ms(False)
+    drift = abs(float(torch.linalg.vector_norm(yc)) - 1.0)
+    ms_ev2, _ = evolve_ms(True)
+    out["evolve_ferrimagnet_chain_n20_c128"] = {
+        "D": D, "t": te, "krylov_m": mk, "ms_per_step_stored_basis": ms_ev, "ms_per_step_rebuilt_basis": ms_ev2,
+        "ms_complex_apply": ms_capply, "complex_gstates_s": D / ms_capply / 1e6,
+        "apply_share_stored": mk * ms_capply / ms_ev, "error_estimate": est, "norm_drift": drift}
+    del xc, yc
+    torch.cuda.empty_cache()
     return out
 
 
