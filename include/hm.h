@@ -16,14 +16,21 @@
  * Vectors: caller-owned DEVICE pointers, state-major interleaved: element v
  * of state k is at [k*nvec + v]. Real storage (HM_F64 / HM_F32) or complex
  * storage (HM_C128 / HM_C64: each element an interleaved (re, im) pair, the
- * layout of C99 double/float _Complex). Every plan holds a real operator (a
- * term list with an imaginary matrix element is rejected when the plan is
- * built), so the real and imaginary parts of a complex vector are applied
- * independently: a complex call with nvec right-hand sides is the real call
- * with 2*nvec interleaved right-hand sides on the same memory (same kernels,
- * same results). hm_apply, hm_apply_ex, hm_apply_adjoint,
- * hm_coupling_gradients_static, hm_batch_apply, hm_tune, hm_tuned_config and
- * hm_lanczos accept complex dtypes; hm_evolve requires one.
+ * layout of C99 double/float _Complex). For a real H the real and imaginary
+ * parts of a complex vector are applied independently: a complex call with
+ * nvec right-hand sides is the real call with 2*nvec interleaved right-hand
+ * sides on the same memory (same kernels, same results); hm_apply,
+ * hm_apply_ex, hm_apply_adjoint, hm_coupling_gradients_static,
+ * hm_batch_apply, hm_tune, hm_tuned_config and hm_lanczos accept complex
+ * dtypes, hm_evolve requires one. A term list with imaginary matrix
+ * elements (Sy factors: a lone Sy, Sx Sy, ...) gives a complex H = H_re +
+ * i H_im, held as two real operators on the same kernels: y = H_re x +
+ * i H_im x costs two real applies of the 2*nvec columns and one combining
+ * pass. Such plans need complex storage (real dtypes give
+ * HM_ERR_COMPLEX_REQUIRED) and support hm_apply, hm_apply_adjoint (gx =
+ * H^dagger gy only), hm_lanczos, hm_evolve, hm_tune, hm_set_coefficients;
+ * hm_apply_ex, coupling gradients, batches and sectors return
+ * HM_ERR_UNSUPPORTED.
  * Every call is asynchronous on the given CUDA stream (NULL = legacy default
  * stream) unless stated otherwise. Plans are library-owned. Applies of one
  * plan (hm_apply, hm_batch_apply) may run on several streams at once: the
@@ -86,7 +93,7 @@ enum {
     HM_ERR_INVALID_ARG = -1,      /* bad site/op kind, i == j, null pointer, nvec < 1 */
     HM_ERR_OVERFLOW = -2,         /* D >= 2^62                                      */
     HM_ERR_ALIAS = -3,            /* x and y overlap                                */
-    HM_ERR_COMPLEX_REQUIRED = -4, /* the term list has an imaginary matrix element  */
+    HM_ERR_COMPLEX_REQUIRED = -4, /* real storage asked of a complex H              */
     HM_ERR_NOT_HERMITIAN = -5,    /* Lanczos on a non-self-adjoint term list        */
     HM_ERR_CUDA = -6,             /* CUDA runtime error (text in hm_last_error)      */
     HM_ERR_OOM = -7,              /* device allocation failed                       */
@@ -99,7 +106,9 @@ enum {
 /* Build a plan (host call; allocates the plan's small device tables on the
  * current device and synchronises). sites[nsites], terms[nterms] are read and
  * copied. Limits: 1 <= nsites <= 64, D = prod d_k < 2^62, each d_k <= 65536.
- * Cost O(N + |terms|) plus O(B) tables for the low-digit block (B <= 8192). */
+ * Cost O(N + |terms|) plus O(B) tables for the low-digit block (B <= 8192).
+ * A term list with imaginary matrix elements builds a complex plan (two real
+ * operators, see Vectors above). */
 int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
               hm_handle* out);
 
@@ -274,7 +283,8 @@ int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);
  * nvec = which >> 8 (at least 1; HM_ERR_UNSUPPORTED if there is no tile
  * form); bit 2: the tables of hm_create_sector for digit_total =
  * which >> 8 (same error codes as hm_create_sector); else the general
- * kernel's. On success *len = bytes needed including
+ * kernel's. bit 3: the imaginary part H_im of a complex H (else H_re, or
+ * the whole real H). On success *len = bytes needed including
  * the terminating NUL; the text is written only if buf != NULL and
  * bufsize >= *len. Same error codes as hm_create. */
 int hm_plan_export(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,

@@ -166,6 +166,41 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
   return HM_OK;
 }
 
+// y_re -= sg t_im, y_im += sg t_re on (re, im) pairs: y = H_re x + sg i H_im x
+// from y = H_re x and t = H_im x
+template <class T>
+__global__ void k_cmix(T* __restrict__ y, const T* __restrict__ t, T sg, long long npairs) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T tr = t[2 * i], ti = t[2 * i + 1];
+    y[2 * i] = y[2 * i] - sg * ti;
+    y[2 * i + 1] = y[2 * i + 1] + sg * tr;
+  }
+}
+
+// Complex H = H_re + i H_im: two real applies on the 2 * nvec (re, im)
+// columns, then one combining pass. The adjoint H^dagger = H_re^T - i H_im^T.
+int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
+  const long long nc = 2 * nvec;
+  int rc = apply_on(p, adjoint, x, y, nc, dt, s, tuned_cfg(p, dt, nc), false);
+  if (rc) return rc;
+  Scratch tb;
+  const long long n = vec_states(p) * nc;
+  rc = scratch_alloc(tb, (size_t)n * (dt == HM_F32 ? 4 : 8), s);
+  if (rc) return rc;
+  rc = apply_on(p->im, adjoint, x, tb.ptr, nc, dt, s, tuned_cfg(p->im, dt, nc), false);
+  if (rc) return rc;
+  const long long np = n / 2;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((np + 255) / 256, (long long)num_sms() * 8));
+  if (dt == HM_F32)
+    k_cmix<float><<<grid, 256, 0, s>>>((float*)y, (const float*)tb.ptr, adjoint ? -1.0f : 1.0f, np);
+  else
+    k_cmix<double><<<grid, 256, 0, s>>>((double*)y, (const double*)tb.ptr, adjoint ? -1.0 : 1.0, np);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "complex combine");
+  return HM_OK;
+}
+
 int launch_apply(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, TuneCfg cfg) {
   return apply_on(p, false, x, y, nvec, dt, s, cfg, false);
 }

@@ -92,6 +92,39 @@ using namespace hm;
 
 extern "C" {
 
+// The companion plan of a complex H (its imaginary part), rebuilt from the
+// current terms; dropped when the term list is real.
+static void destroy_plan(Plan* p);
+static int build_companion(Plan* p) {
+  if (!p->complex_h) {
+    if (p->im) destroy_plan(p->im);
+    p->im = nullptr;
+    return HM_OK;
+  }
+  if (!p->im) {
+    p->im = new Plan();
+    p->im->N = p->N;
+    p->im->sites = p->sites;
+    p->im->device = p->device;
+    p->im->part = 1;
+  }
+  p->im->terms = p->terms;
+  return build_plan(p->im);
+}
+
+static int complex_only(const Plan* p, const char* what) {
+  if (p && p->im) {
+    set_error(std::string(what) + " is not available for a complex H (imaginary matrix elements)");
+    return HM_ERR_UNSUPPORTED;
+  }
+  return HM_OK;
+}
+
+static int needs_complex_storage() {
+  set_error("the term list has imaginary matrix elements (e.g. a lone Sy): use HM_C128 or HM_C64 storage");
+  return HM_ERR_COMPLEX_REQUIRED;
+}
+
 int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
               hm_handle* out) {
   if (!out) { set_error("out is NULL"); return HM_ERR_INVALID_ARG; }
@@ -108,9 +141,9 @@ int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_
   cudaGetDevice(&p->device);
   int rc = plan_check(p);
   if (rc == HM_OK) rc = build_plan(p);
+  if (rc == HM_OK) rc = build_companion(p);
   if (rc != HM_OK) {
-    free_plan_device(p);
-    delete p;
+    destroy_plan(p);
     return rc;
   }
   *out = reinterpret_cast<hm_handle>(p);
@@ -135,6 +168,10 @@ int hm_create_sector(const hm_site* sites, int32_t nsites, const hm_term* terms,
   cudaGetDevice(&p->device);
   int rc = plan_check(p);
   if (rc == HM_OK) rc = build_plan(p);   // builds the sector tables too
+  if (rc == HM_OK && p->complex_h) {
+    set_error("complex term lists (imaginary matrix elements) are not available for sector plans");
+    rc = HM_ERR_UNSUPPORTED;
+  }
   if (rc != HM_OK) {
     free_plan_device(p);
     free_sector(p);
@@ -163,9 +200,11 @@ int hm_set_coefficients(hm_handle h, const double* coefs) {
   std::vector<hm_term> old = p->terms;
   for (size_t t = 0; t < p->terms.size(); ++t) p->terms[t].coef = coefs[t];
   int rc = build_plan(p);
+  if (rc == HM_OK) rc = build_companion(p);
   if (rc != HM_OK) {
     p->terms = old;
     int rc2 = build_plan(p);
+    if (rc2 == HM_OK) rc2 = build_companion(p);
     (void)rc2;
   }
   return rc;
@@ -185,10 +224,12 @@ int32_t hm_num_terms(hm_handle h) {
 
 int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
+  const bool cx = dtype == HM_C128 || dtype == HM_C64;
   long long nvec = nvec_in;
   real_view(dtype, nvec);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
+  if (p->im) return cx ? apply_complex(p, false, x, y, nvec / 2, dtype, (cudaStream_t)stream) : needs_complex_storage();
   if (p->sector) return launch_sector(p, x, y, nvec, dtype, (cudaStream_t)stream);
   return launch_apply(p, x, y, nvec, dtype, (cudaStream_t)stream, tuned_cfg(p, dtype, nvec));
 }
@@ -201,6 +242,7 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
   if ((rc = no_sector(p, "hm_apply_ex"))) return rc;
+  if ((rc = complex_only(p, "hm_apply_ex"))) return rc;
   TuneCfg cfg;
   cfg.ctas = ctas > 0 ? ctas : 0;
   cfg.mb = (flags >> 2) & 1;
@@ -227,10 +269,22 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
                      int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
+  const bool cx = dtype == HM_C128 || dtype == HM_C64;
   long long nvec = nvec_in;
   real_view(dtype, nvec);
   if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
   if (int rc = no_sector(p, "hm_apply_adjoint")) return rc;
+  if (p->im) {  // complex H: gx = H^dagger gy only
+    if (gcoef) {
+      set_error("coupling gradients are not available for a complex H");
+      return HM_ERR_UNSUPPORTED;
+    }
+    if (!gx) return HM_OK;
+    if (!cx) return needs_complex_storage();
+    int rc = check_vec_args(p, gy, gx, nvec, dtype);
+    if (rc) return rc;
+    return apply_complex(p, true, gy, gx, nvec / 2, dtype, (cudaStream_t)stream);
+  }
   if (!gx && !gcoef) return HM_OK;
   if (gx) {
     int rc = check_vec_args(p, gy, gx, nvec, dtype);
@@ -256,7 +310,8 @@ int hm_lanczos(hm_handle h, const void* v0, int32_t steps, hm_dtype dtype, int32
   long long nvec = 1;
   real_view(dtype, nvec);
   if (dtype != HM_F64 && dtype != HM_F32) { set_error("bad dtype"); return HM_ERR_INVALID_ARG; }
-  if (!p->hermitian) {
+  if (p->im && nvec != 2) return needs_complex_storage();
+  if (!p->hermitian_c) {
     set_error("Lanczos needs a self-adjoint term list");
     return HM_ERR_NOT_HERMITIAN;
   }
@@ -273,7 +328,7 @@ int hm_batch_create(const hm_handle* hs, int32_t n, hm_handle* batch_out) {
   b->is_batch = true;
   for (int i = 0; i < n; ++i) {
     Plan* p = as_plan(hs[i]);
-    if (!p || p->is_batch || p->sector) {
+    if (!p || p->is_batch || p->sector || p->im) {
       delete b;
       set_error("batch member " + std::to_string(i) + " is not a full-basis plan handle");
       return HM_ERR_INVALID_ARG;
@@ -309,16 +364,22 @@ int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int6
   return launch_batch(b, xs, ys, nvec, dtype, (cudaStream_t)stream);
 }
 
-int hm_destroy(hm_handle h) {
-  Plan* p = as_plan(h);
-  if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
-  cudaDeviceSynchronize();
+static void destroy_plan(Plan* p) {
+  if (p->im) destroy_plan(p->im);
+  p->im = nullptr;
   free_plan_device(p);
   free_tiles(p);
   free_sector(p);
   if (p->scratch) cudaFree(p->scratch);
   p->magic = 0;
   delete p;
+}
+
+int hm_destroy(hm_handle h) {
+  Plan* p = as_plan(h);
+  if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
+  cudaDeviceSynchronize();
+  destroy_plan(p);
   scratch_trim();
   return HM_OK;
 }
@@ -340,6 +401,15 @@ int hm_tune(hm_handle h, int64_t nvec_in, hm_dtype dtype, void* stream) {
     return HM_ERR_INVALID_ARG;
   }
   if (int rc = no_sector(p, "hm_tune")) return rc;
+  if (p->im) {  // complex H: tune both real parts for the 2 * nvec columns
+    p->im->tuned.clear();
+    Plan* q = p->im;
+    p->im = nullptr;
+    int rc = hm_tune(reinterpret_cast<hm_handle>(p), nvec, dtype, stream);
+    if (rc == HM_OK) rc = hm_tune(reinterpret_cast<hm_handle>(q), nvec, dtype, stream);
+    p->im = q;
+    return rc;
+  }
   const std::string sig = tune_signature(p, dtype, nvec);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -455,7 +525,7 @@ int hm_evolve(hm_handle h, const void* x, void* y, double t, int32_t m, int32_t 
   real_view(dtype, nvec);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
-  if (!p->hermitian) {
+  if (!p->hermitian_c) {
     set_error("time evolution needs a self-adjoint term list");
     return HM_ERR_NOT_HERMITIAN;
   }

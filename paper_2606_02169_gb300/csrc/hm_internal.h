@@ -216,6 +216,14 @@ struct Plan {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
 
+  // complex H = H_re + i H_im (imaginary matrix elements from Sy factors):
+  // this plan holds H_re (part 0), `im` the companion plan holding H_im
+  // (part 1); both are real operators on the kernels above
+  int part = 0;
+  bool complex_h = false;     // the term list has imaginary matrix elements
+  bool hermitian_c = false;   // H^dagger = H for the complex operator
+  Plan* im = nullptr;
+
   // fixed digit-sum sector (hm_create_sector): vectors hold the Dsec
   // retained states instead of all D
   bool sector = false;
@@ -299,6 +307,9 @@ int scratch_alloc(Scratch& b, size_t bytes, cudaStream_t s);
 void scratch_trim();
 // n FP64 values split into float pairs in fresh scratch `b`
 int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out);
+// y = H x (or H^dagger x when adjoint) for nvec complex right-hand sides of a
+// complex plan, dt the real type of the (re, im) pairs
+int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
 // Lanczos on vectors of vec_states * nvec elements of the real dtype dt

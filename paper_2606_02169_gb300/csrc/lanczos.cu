@@ -298,8 +298,10 @@ static std::vector<double> lowest_eigvec(const std::vector<double>& a, const std
 
 // Work vectors, device scalars and launch shapes of one Lanczos recurrence on
 // vectors of n = states * nvec elements (nvec = 2: the real and imaginary
-// parts of a complex vector, interleaved; for a real H the recurrence on the
-// pairs is the complex recurrence, whose alpha and beta are real).
+// parts of a complex vector, interleaved). For a self-adjoint H, alpha =
+// <v, H v> and beta = |w| are real, and the real dot products of the pairs
+// are the real parts of the complex ones, so the recurrence on the pairs is
+// the complex recurrence (for a complex H the apply is the complex one).
 template <class T>
 struct Recurrence {
   Plan* p = nullptr;
@@ -362,7 +364,8 @@ struct Recurrence {
     for (int k = 0; k < m; ++k) {
       int arc = at_step(k, (const T*)vk);
       if (arc) return arc;
-      arc = apply_on(p, false, vk, w, nvec, dt, s, tuned_cfg(p, dt, nvec), false);
+      arc = p->im ? apply_complex(p, false, vk, w, nvec / 2, dt, s)  // complex H: nvec = 2
+                  : apply_on(p, false, vk, w, nvec, dt, s, tuned_cfg(p, dt, nvec), false);
       if (arc) return arc;
       dot(vk, w, dal + k, 0);
       const T* vpk = k > 0 ? vp : nullptr;

@@ -224,6 +224,73 @@ static bool is_symmetric(const std::vector<Channel>& ch) {
   return true;
 }
 
+// H^dagger = H: every channel's transpose equals the complex conjugate of
+// the channel with the transposed shifts.
+static bool is_self_adjoint(const std::vector<Channel>& ch) {
+  std::map<std::tuple<int, int, int, int>, const Channel*> idx;
+  double mx = 0.0;
+  for (auto& c : ch) {
+    idx[std::make_tuple(c.i, c.qi, c.j, c.qj)] = &c;
+    for (auto& v : c.T) mx = std::max(mx, std::abs(v));
+  }
+  for (auto& c : ch) {
+    Channel t = transpose_channel(c);
+    auto it = idx.find(std::make_tuple(t.i, t.qi, t.j, t.qj));
+    bool zero_t = std::all_of(t.T.begin(), t.T.end(), [](cplx v) { return v == cplx(0, 0); });
+    if (it == idx.end()) {
+      if (!zero_t) return false;
+      continue;
+    }
+    for (size_t e = 0; e < t.T.size(); ++e)
+      if (std::abs(t.T[e] - std::conj(it->second->T[e])) > 1e-12 * (1.0 + mx)) return false;
+  }
+  return true;
+}
+
+// A complex H = H_re + i H_im is held as two real operators on the same
+// channel structure: keep the real (part 0) or imaginary (part 1) part of
+// every table, and split each contributing product a (x) b so that the
+// factor lists still sum to the kept table:
+//   Re(a (x) b) = Re a (x) Re b - Im a (x) Im b,
+//   Im(a (x) b) = Re a (x) Im b + Im a (x) Re b.
+// Channels whose kept part vanishes are dropped.
+static void keep_part(std::vector<Channel>& ch, int part) {
+  auto re = [](const std::vector<cplx>& v, double sg) {
+    std::vector<cplx> r(v.size());
+    for (size_t i = 0; i < v.size(); ++i) r[i] = sg * v[i].real();
+    return r;
+  };
+  auto im = [](const std::vector<cplx>& v) {
+    std::vector<cplx> r(v.size());
+    for (size_t i = 0; i < v.size(); ++i) r[i] = v[i].imag();
+    return r;
+  };
+  auto zero = [](const std::vector<cplx>& v) {
+    return std::all_of(v.begin(), v.end(), [](cplx z) { return z == cplx(0, 0); });
+  };
+  std::vector<Channel> out;
+  for (Channel c : ch) {
+    for (auto& v : c.T) v = part ? cplx(v.imag(), 0.0) : cplx(v.real(), 0.0);
+    if (zero(c.T)) continue;
+    std::vector<std::pair<std::vector<cplx>, std::vector<cplx>>> np;
+    for (auto& pr : c.parts) {
+      std::pair<std::vector<cplx>, std::vector<cplx>> u, w;
+      if (part == 0) {
+        u = {re(pr.first, 1.0), re(pr.second, 1.0)};
+        w = {re(im(pr.first), -1.0), im(pr.second)};
+      } else {
+        u = {re(pr.first, 1.0), im(pr.second)};
+        w = {im(pr.first), re(pr.second, 1.0)};
+      }
+      for (auto* q : {&u, &w})
+        if (!zero(q->first) && !zero(q->second)) np.push_back(*q);
+    }
+    c.parts = np;
+    out.push_back(std::move(c));
+  }
+  ch.swap(out);
+}
+
 // Device-table assembly for one operator (H or H^T) under the plan's split.
 struct HostTables {
   std::vector<KChan> kch;       // [HH diag | HH off-diagonal]
@@ -572,11 +639,18 @@ int derive_plan(Plan* p, HostPlanData& out) {
     set_error("operator expansion failed");
     return rc;
   }
-  if (!all_real(dv)) {
-    set_error("the term list has imaginary matrix elements (e.g. a lone Sy); real storage cannot hold it");
-    return HM_ERR_COMPLEX_REQUIRED;
+  p->complex_h = !all_real(dv);
+  if (p->complex_h) {  // imaginary matrix elements (Sy factors): keep one part
+    p->hermitian_c = is_self_adjoint(dv.ch);
+    keep_part(dv.ch, p->part);
+    dv.tch.clear();    // coupling gradients are not provided for complex H
+    dv.tch_term.clear();
+  } else if (p->part == 1) {
+    dv.ch.clear();     // the imaginary part of a real H
   }
+  if (p->part == 1) dv.constant = 0.0;  // coefficients are real: constants are real
   p->hermitian = is_symmetric(dv.ch);
+  if (!p->complex_h) p->hermitian_c = p->hermitian;
 
   build_tables(p, dv.ch, dv.constant, ptab, ks, Hf);
   std::vector<Channel> tr;
@@ -783,6 +857,10 @@ int export_plan(Plan* p, int which, std::string& o) {
   HostPlanData hd;
   int rc = derive_plan(p, hd);
   if (rc) return rc;
+  if ((which & 4) && p->complex_h) {
+    set_error("complex term lists (imaginary matrix elements) are not available for sector plans");
+    return HM_ERR_UNSUPPORTED;
+  }
   if (which & 4) {  // sector tables for the digit total which >> 8
     o = export_sector_json(p, which >> 8, &rc);
     return rc;
@@ -793,7 +871,7 @@ int export_plan(Plan* p, int which, std::string& o) {
     o = export_tile_json(p, tr ? p->chT : p->chH, p->constant, nvec, &rc);
     return rc;
   }
-  const HostTables& H = (which == 1 && !p->hermitian) ? hd.Ht : hd.Hf;
+  const HostTables& H = ((which & 1) && !p->hermitian) ? hd.Ht : hd.Hf;
   auto I = [&](long long v) { o += std::to_string(v); };
   o = "{";
   o += "\"D\":" + std::to_string(p->D) + ",\"B\":" + std::to_string(p->B) + ",\"nblk\":" + std::to_string(p->nblk) +
@@ -838,6 +916,7 @@ extern "C" int hm_plan_export(const hm_site* sites, int32_t nsites, const hm_ter
   p.N = nsites;
   p.sites.assign(sites, sites + nsites);
   p.terms.assign(terms, terms + nterms);
+  p.part = (which >> 3) & 1;  // bit 3: the imaginary part of a complex H
   int rc = plan_check(&p);
   if (rc) return rc;
   std::string o;

@@ -245,14 +245,17 @@ def test_alias_and_dtype_errors():
         h.apply(x.to(torch.float16))
 
 
-def test_complex_term_list_rejected():
-    torch_cuda()
+def test_complex_term_list_needs_complex_storage():
+    torch = torch_cuda()
     from paper_2606_02169_gb300 import HmError, _capi as C, Hamiltonian
+    h = Hamiltonian([("spin", 3)], [(0, "Sy", -1, "I", 1.0)])   # imaginary elements: a complex plan
     with pytest.raises(HmError) as e:
-        Hamiltonian([("spin", 3)], [(0, "Sy", -1, "I", 1.0)])
+        h.apply(torch.zeros(3, dtype=torch.float64, device="cuda"))
     assert e.value.code == C.HM_ERR_COMPLEX_REQUIRED
-    # SySy is real and accepted
-    Hamiltonian([("spin", 3), ("spin", 2)], [(0, "Sy", 1, "Sy", 1.0)])
+    h.apply(torch.zeros(3, dtype=torch.complex128, device="cuda"))
+    # SySy is real and takes real storage
+    Hamiltonian([("spin", 3), ("spin", 2)], [(0, "Sy", 1, "Sy", 1.0)]).apply(
+        torch.zeros(6, dtype=torch.float64, device="cuda"))
 
 
 def test_set_coefficients_matches_fresh_plan():

@@ -228,3 +228,119 @@ def test_evolve_errors():
     z = torch.zeros_like(x)
     y, err = h.evolve(z, 0.3)
     assert float(torch.linalg.vector_norm(y)) == 0.0 and err == 0.0
+
+
+# ---------------------------------------------------------------------------
+# complex H (imaginary matrix elements from Sy factors)
+# ---------------------------------------------------------------------------
+
+def _dm_chain(n=7, d=2, J=1.0, Dm=0.45, hy=0.3, seed=0):
+    """Heisenberg chain with a Dzyaloshinskii-Moriya term D (Sx_i Sy_j - Sy_i
+    Sx_j) and a transverse Sy field: Hermitian, with imaginary elements."""
+    rng = np.random.default_rng(seed)
+    sites = [("spin", d)] * n
+    terms = []
+    for i in range(n - 1):
+        j = i + 1
+        terms += [(i, "Sx", j, "Sx", J), (i, "Sy", j, "Sy", J), (i, "Sz", j, "Sz", J * 0.8),
+                  (i, "Sx", j, "Sy", Dm), (i, "Sy", j, "Sx", -Dm)]
+    for i in range(n):
+        terms += [(i, "Sy", -1, "I", hy * rng.uniform(0.5, 1.5)), (i, "Sz", -1, "I", 0.2 * rng.normal())]
+    return sites, terms
+
+
+CX_MODELS = [_dm_chain(7, 2, seed=1), _dm_chain(5, 3, seed=2),
+             ([("spin", 2), ("boson", 4), ("spin", 3)],
+              [(0, "Sy", 1, "N", 0.7), (2, "Sy", -1, "I", 0.4), (0, "Sm", 1, "adag", 0.5), (0, "Sp", 1, "a", 0.5),
+               (2, "Sx", 0, "Sy", 0.3), (1, "N", -1, "I", 1.1)])]
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+@pytest.mark.parametrize("cdt,tol", [("complex128", TOL_F64), ("complex64", TOL_F32)])
+@pytest.mark.parametrize("nvec", [1, 2])
+def test_complex_h_apply_matches_oracle(case, cdt, tol, nvec):
+    torch = torch_cuda()
+    sites, terms = CX_MODELS[case]
+    h = _ham(sites, terms)
+    x = _cx(h.D, 13, nvec)
+    xt = torch.from_numpy(x).to("cuda", getattr(torch, cdt))
+    y = h.apply(xt).cpu().numpy()
+    xr = xt.cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(sites, terms, xr, nvec=nvec)
+    H = abs(oracle.dense(sites, terms, sparse=True))
+    scale = np.asarray(H @ np.abs(xr).reshape(h.D, nvec)).reshape(-1)
+    assert np.abs(ref.imag).max() > 0
+    _close(y, ref, scale, tol, f"complex H case {case} {cdt}")
+
+
+def test_complex_h_adjoint_is_the_conjugate_transpose():
+    torch = torch_cuda()
+    sites = [("spin", 2), ("spin", 3), ("spin", 2)]
+    terms = [(0, "Sy", 1, "Sp", 0.7), (1, "Sy", -1, "I", -0.4), (0, "Sx", 2, "Sy", 0.5), (2, "Sm", -1, "I", 0.3)]
+    h = _ham(sites, terms)                   # not self-adjoint
+    gy = _cx(h.D, 17)
+    gx, _ = h.adjoint(torch.from_numpy(gy).cuda(), want_gcoef=False)
+    Hd = oracle.dense(sites, terms).conj().T
+    assert np.allclose(gx.cpu().numpy(), Hd @ gy, rtol=0, atol=1e-13)
+
+
+def test_complex_h_lanczos_and_evolution():
+    torch = torch_cuda()
+    sites, terms = CX_MODELS[0]
+    h = _ham(sites, terms)
+    H = oracle.dense(sites, terms)
+    assert np.abs(H - H.conj().T).max() < 1e-14 and np.abs(H.imag).max() > 0
+    e_exact = np.linalg.eigvalsh(H)[0]
+    r = h.lanczos(torch.from_numpy(_cx(h.D, 19)).cuda(), 100, reorth=True, ritz_vector=True)
+    assert abs(r["e0"] - e_exact) < 1e-9 * abs(e_exact)
+    psi = r["psi0"]
+    assert float(torch.linalg.vector_norm(h.apply(psi) - r["e0"] * psi)) < 1e-6
+    x = _cx(h.D, 23)
+    for cdt, tol in (("complex128", 1e-10), ("complex64", 2e-5)):
+        xt = torch.from_numpy(x).to("cuda", getattr(torch, cdt))
+        y, err = h.evolve(xt, 1.3, m=30, substeps=3)
+        ref = oracle.evolve(sites, terms, xt.cpu().numpy().astype(np.complex128), 1.3)
+        assert np.linalg.norm(y.cpu().numpy() - ref) <= tol * np.linalg.norm(ref), cdt
+
+
+def test_complex_h_coefficient_updates_and_tuning():
+    torch = torch_cuda()
+    sites, terms = CX_MODELS[1]
+    h = _ham(sites, terms)
+    x = torch.from_numpy(_cx(h.D, 29)).cuda()
+    # switch every Sy-carrying coefficient off: the plan becomes real
+    c0 = [t[4] for t in terms]
+    c1 = [0.0 if "Sy" in (t[1], t[3]) and not (t[1] == "Sy" and t[3] == "Sy") else t[4] for t in terms]
+    h.set_coefficients(c1)
+    real_terms = [(t[0], t[1], t[2], t[3], c) for t, c in zip(terms, c1)]
+    h.apply(torch.zeros(h.D, dtype=torch.float64, device="cuda"))          # real storage works again
+    assert torch.equal(h.apply(x), _ham(sites, real_terms).apply(x))
+    h.set_coefficients(c0)
+    assert torch.equal(h.apply(x), _ham(sites, terms).apply(x))
+    h.tune(1, torch.complex128)
+    ref = oracle.apply(sites, terms, x.cpu().numpy())
+    assert np.allclose(h.apply(x).cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_complex_h_errors():
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Batch, HmError, _capi as C
+    sites, terms = CX_MODELS[0]
+    h = _ham(sites, terms)
+    xr = torch.zeros(h.D, dtype=torch.float64, device="cuda")
+    xc = torch.zeros(h.D, dtype=torch.complex128, device="cuda")
+    with pytest.raises(HmError) as e:
+        h.apply(xr)
+    assert e.value.code == C.HM_ERR_COMPLEX_REQUIRED
+    with pytest.raises(HmError) as e:
+        h.apply_ex(xc)
+    assert e.value.code == C.HM_ERR_UNSUPPORTED
+    with pytest.raises(HmError) as e:
+        h.adjoint(xc, xc)
+    assert e.value.code == C.HM_ERR_UNSUPPORTED
+    with pytest.raises(HmError) as e:
+        Batch([h])
+    assert e.value.code == C.HM_ERR_INVALID_ARG
+    with pytest.raises(HmError) as e:
+        _ham(sites, terms, 3)
+    assert e.value.code in (C.HM_ERR_UNSUPPORTED,)

@@ -55,6 +55,31 @@ def test_imaginary_factors_with_real_product(capi):
     assert np.allclose(emulate(P, x), ref, rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("dims,kinds", CASES[:4] + CASES[5:])
+@pytest.mark.parametrize("seed", [3, 4])
+def test_complex_h_as_two_real_plans(capi, dims, kinds, seed):
+    """A term list with imaginary matrix elements (Sy factors): the exported
+    real-part plan (which = 0) and imaginary-part plan (bit 3) give
+    H = H_re + i H_im, and their transposes (bit 0) give H^T, against the
+    oracle's complex Kronecker assembly."""
+    m = W.random_model(list(dims), kinds, nterms=20, seed=seed)
+    spins = [k for k, (kind, _) in enumerate(m.sites) if kind in ("spin", 0)]
+    a, b = spins[0], spins[-1]
+    terms = m.terms + [(a, "Sy", -1, "I", 0.6), (a, "Sx", b, "Sy", -0.4), (b, "Sy", a, "Sz", 0.3),
+                       (b, "Sy", -1, "I", -0.2 * seed)]
+    m = W.Model(m.name + "+Sy", m.sites, terms)
+    D = oracle.dimension(m.sites)
+    H = oracle.dense(m.sites, m.terms, sparse=True)
+    assert abs(H.imag).max() > 0
+    x = W.vector(D, 7) + 1j * W.vector(D, 8)
+    for tr, M in ((0, H), (1, H.T)):
+        Pr = capi.plan_export(m.sites, m.terms, tr)
+        Pi = capi.plan_export(m.sites, m.terms, tr | 8)
+        y = (emulate(Pr, x.real) - emulate(Pi, x.imag)) + 1j * (emulate(Pr, x.imag) + emulate(Pi, x.real))
+        ref = np.asarray(M @ x)
+        assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref), tr
+
+
 def test_workload_plans(capi):
     """Split and channel structure of the workload shapes."""
     P = capi.plan_export(*_m(W.tavis_cummings(24, 64, seed=7)))
