@@ -175,7 +175,9 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtyp
  * plan-owned scratch of O(nterms * grid) doubles, grown on demand (so the
  * first call of a size should come before any stream capture) and, for
  * HM_F64, per-call pool scratch as in hm_apply for gy and x split once.
- * Calls on the same plan must not overlap on the GPU. */
+ * Calls on the same plan must not overlap on the GPU. gcoef gives
+ * HM_ERR_UNSUPPORTED when a term's own operator has imaginary elements
+ * (its real gradient is undefined), e.g. a Sy term with zero coefficient. */
 int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, double* gcoef,
                      int64_t nvec, hm_dtype dtype, void* stream);
 

@@ -290,6 +290,10 @@ int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, doubl
     int rc = check_vec_args(p, gy, gx, nvec, dtype);
     if (rc) return rc;
   }
+  if (gcoef && !p->grad_ok) {
+    set_error("a term of this list has imaginary matrix elements: its coupling gradient is undefined");
+    return HM_ERR_UNSUPPORTED;
+  }
   if (gcoef) {
     int rc = check_vec_args(p, gy, x ? x : gy, nvec, dtype);
     if (rc == HM_ERR_ALIAS) rc = HM_OK;  // gy and x may be the same vector

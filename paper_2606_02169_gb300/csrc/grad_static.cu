@@ -66,8 +66,8 @@ extern "C" int hm_coupling_gradients_static(hm_handle h, const void* gy, const v
     set_error("hm_coupling_gradients_static is not available for sector plans (hm_create_sector)");
     return HM_ERR_UNSUPPORTED;
   }
-  if (p->im) {
-    set_error("coupling gradients are not available for a complex H");
+  if (p->im || !p->grad_ok) {
+    set_error("coupling gradients are not available for a complex H or a term with imaginary elements");
     return HM_ERR_UNSUPPORTED;
   }
   if (!gy || !x || !gcoef || nvec < 1 || (dtype != HM_F64 && dtype != HM_F32)) {

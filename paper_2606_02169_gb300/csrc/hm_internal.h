@@ -223,6 +223,7 @@ struct Plan {
   bool complex_h = false;     // the term list has imaginary matrix elements
   bool hermitian_c = false;   // H^dagger = H for the complex operator
   Plan* im = nullptr;
+  bool grad_ok = true;        // every term's operator is real (coupling gradients defined)
 
   // fixed digit-sum sector (hm_create_sector): vectors hold the Dsec
   // retained states instead of all D

@@ -639,12 +639,14 @@ int derive_plan(Plan* p, HostPlanData& out) {
     set_error("operator expansion failed");
     return rc;
   }
+  p->grad_ok = true;
   p->complex_h = !all_real(dv);
   if (p->complex_h) {  // imaginary matrix elements (Sy factors): keep one part
     p->hermitian_c = is_self_adjoint(dv.ch);
     keep_part(dv.ch, p->part);
     dv.tch.clear();    // coupling gradients are not provided for complex H
     dv.tch_term.clear();
+    p->grad_ok = false;
   } else if (p->part == 1) {
     dv.ch.clear();     // the imaginary part of a real H
   }
@@ -674,17 +676,19 @@ int derive_plan(Plan* p, HostPlanData& out) {
     k.term = dv.tch_term[c];
     k.si = (uint8_t)ch.i;
     k.sj = (uint8_t)(ch.j >= 0 ? ch.j : 255);
-    // per-term tables may be complex (a lone Sy); gradients need the real
-    // part only when the full term list is real, which all_real enforced
-    // for the merged operator, but a single term of a real sum (SySy) is
-    // itself real. An imaginary per-term table (pair of canceling Sy terms)
-    // is rejected.
+    // A term of a real H may itself be imaginary (a Sy term whose
+    // coefficient is zero, or two that cancel): its operator O_t has no real
+    // gradient, so the plan then offers no coupling gradients at all.
+    bool term_real = true;
     for (auto& v : ch.T) {
-      if (std::abs(v.imag()) > 1e-13 * (1.0 + std::abs(v))) {
-        set_error("a single term has imaginary matrix elements; real gradients are undefined");
-        return HM_ERR_COMPLEX_REQUIRED;
-      }
+      term_real = term_real && std::abs(v.imag()) <= 1e-13 * (1.0 + std::abs(v));
       ttab.push_back(v.real());
+    }
+    if (!term_real) {
+      p->grad_ok = false;
+      tk.clear();
+      ttab.clear();
+      break;
     }
     tk.push_back(k);
   }

@@ -315,6 +315,10 @@ def test_complex_h_coefficient_updates_and_tuning():
     real_terms = [(t[0], t[1], t[2], t[3], c) for t, c in zip(terms, c1)]
     h.apply(torch.zeros(h.D, dtype=torch.float64, device="cuda"))          # real storage works again
     assert torch.equal(h.apply(x), _ham(sites, real_terms).apply(x))
+    from paper_2606_02169_gb300 import HmError, _capi as C
+    with pytest.raises(HmError) as e:           # the zeroed Sy terms have no real gradient
+        h.adjoint(x, x)
+    assert e.value.code == C.HM_ERR_UNSUPPORTED
     h.set_coefficients(c0)
     assert torch.equal(h.apply(x), _ham(sites, terms).apply(x))
     h.tune(1, torch.complex128)
