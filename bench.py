@@ -646,6 +646,32 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
         "apply_share_stored": mk * ms_capply / ms_ev, "error_estimate": est, "norm_drift": drift}
     del xc, yc
     torch.cuda.empty_cache()
+
+    # complex H: periodic spin-1/2 chain N = 26 with a Dzyaloshinskii-Moriya
+    # term and a transverse Sy field (imaginary elements), complex128,
+    # beside the same chain without the imaginary terms (real H, complex x)
+    nd = 26
+    sd = [("spin", 2)] * nd
+    real_t, cx_t = [], []
+    for i in range(nd):
+        j = (i + 1) % nd
+        a, b = min(i, j), max(i, j)
+        real_t += [(a, "Sx", b, "Sx", 1.0), (a, "Sy", b, "Sy", 1.0), (a, "Sz", b, "Sz", 0.8)]
+        cx_t += [(a, "Sx", b, "Sy", 0.3), (a, "Sy", b, "Sx", -0.3), (i, "Sy", -1, "I", 0.2)]
+    res = {}
+    for name, terms in (("complex_h", real_t + cx_t), ("real_h", real_t)):
+        hd = Hamiltonian(sd, terms)
+        if args.tune:
+            hd.tune(1, torch.complex128)
+        xd = torch.complex(W.torch_vector(hd.D, 24, dtype=torch.float64), W.torch_vector(hd.D, 25, dtype=torch.float64))
+        yd = torch.empty_like(xd)
+        k = 10
+        res[name] = timed(lambda: hd.apply(xd, out=yd), k, 3, 1, stream) / k
+        del hd, xd, yd
+        torch.cuda.empty_cache()
+    out["complex_h_dm_chain_n26_c128"] = {
+        "D": 2 ** nd, "ms_complex_h": res["complex_h"], "gstates_s_complex_h": 2 ** nd / res["complex_h"] / 1e6,
+        "ms_real_h_complex_x": res["real_h"], "complex_h_over_real_h": res["complex_h"] / res["real_h"]}
     return out
 
 
