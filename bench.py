@@ -56,8 +56,21 @@ def parse():
     return ap.parse_args()
 
 
+def _ring_sector(n):
+    """Periodic spin-1/2 Heisenberg chain of n sites restricted to M = 0 (the
+    fixed digit-sum sector with total n / 2)."""
+    import workloads as W
+    terms = []
+    for i in range(n):
+        j = (i + 1) % n
+        terms += [(i, "Sp", j, "Sm", 0.5), (i, "Sm", j, "Sp", 0.5), (i, "Sz", j, "Sz", 1.0)]
+    return W.Model(f"sector_chain_n{n}_m0", [("spin", 2)] * n, terms, {"sector_total": n // 2})
+
+
 def _workload(name):
     import workloads as W
+    if name.startswith("sector_chain_n"):
+        return _ring_sector(int(name[len("sector_chain_n"):].split("_")[0]))
     return {
         "ferrimagnet_chain_n20": lambda: W.ferrimagnet_chain(20),
         "tavis_cummings_n20_l64": lambda: W.tavis_cummings(20, 64, seed=7),
@@ -68,7 +81,7 @@ def _workload(name):
 
 
 PROFILE_WORKLOADS = {"ferrimagnet_chain_n20", "tavis_cummings_n20_l64", "tavis_cummings_n24_l64",
-                     "square_lattice_4x5", "heisenberg_ring_n12"}
+                     "square_lattice_4x5", "heisenberg_ring_n12", "sector_chain_n26_m0", "sector_chain_n30_m0"}
 
 
 def run_profile(args):
@@ -78,9 +91,10 @@ def run_profile(args):
     import workloads as W
     from paper_2606_02169_gb300 import Hamiltonian
     m = _workload(args.workload)
-    h = Hamiltonian(m.sites, m.terms)
+    total = m.meta.get("sector_total")
+    h = Hamiltonian(m.sites, m.terms, sector_total=total)
     dt = torch.float64 if args.dtype == "f64" else torch.float32
-    cfg = h.tune(1, dt) if args.tune and args.kernel == "auto" else None
+    cfg = h.tune(1, dt) if args.tune and args.kernel == "auto" and total is None else None
     x = W.torch_vector(h.D, 3, dtype=dt)
     y = torch.empty_like(x)
     if args.kernel == "auto":
@@ -671,6 +685,7 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
         torch.cuda.empty_cache()
     out["complex_h_dm_chain_n26_c128"] = {
         "D": 2 ** nd, "ms_complex_h": res["complex_h"], "gstates_s_complex_h": 2 ** nd / res["complex_h"] / 1e6,
+        "hbm_frac_algorithmic": 32 * 2 ** nd / res["complex_h"] / 1e6 / hbm,
         "ms_real_h_complex_x": res["real_h"], "complex_h_over_real_h": res["complex_h"] / res["real_h"]}
     return out
 

@@ -101,8 +101,13 @@ __device__ __forceinline__ void sector_rows(const KSector& S, const SecTabs<type
   using P = SecAr<AR>;
   using C = typename P::C;
   using TX = typename P::TX;
-  const int N = S.N, K1 = S.K + 1, nch = S.nch;
+  const int N = S.N, K1 = S.K + 1, nch = S.nch, ndiag = S.ndiag;
   const int t = threadIdx.x;
+  // row index of a state (32-bit when the sector has fewer than 2^31 states)
+  auto at = [&](DT row, int v0) -> size_t {
+    const size_t r = sizeof(DT) == 4 ? (size_t)(unsigned)row : (size_t)row;
+    return NV == 1 ? r : r * (size_t)nvec + v0;
+  };
   auto Aat = [&](int k, int tt, int n) { return G.A[G.Aoff[k] + tt * (G.d[k] + 1) + n]; };
   for (long long F = blockIdx.x * (long long)kSecNT + t; F < S.Dsec; F += (long long)gridDim.x * kSecNT) {
     // 1. unrank: digit m at site k is the first whose block of states
@@ -124,46 +129,51 @@ __device__ __forceinline__ void sector_rows(const KSector& S, const SecTabs<type
       dr[k * kSecNT + t] = (unsigned short)(m | (left << 8));
       left -= m;
     }
-    // 2.-4. channels, up to 8 right-hand sides per pass; the diagonal
-    // channels' coefficients are summed first and multiply x_F once
+    // 2.-4. channels, up to 8 right-hand sides per pass: first the diagonal
+    // ones (their coefficients are summed and multiply x_F once), then the
+    // moves
+    const DT Fd = (DT)F;
     for (int v0 = 0; v0 < nvec; v0 += (NV ? NV : 8)) {
       const int nv = NV ? NV : min(8, nvec - v0);
       typename P::Acc acc[8];
       for (int v = 0; v < nv; ++v) acc[v] = P::zero();
       typename P::Acc dsum = P::zero();
-      for (int c = 0; c < nch; ++c) {
+      for (int c = 0; c < ndiag; ++c) {
+        const KSecChan ch = G.ch[c];
+        const int ni = sec_digit(dr[ch.si * kSecNT + t]);
+        const int nj = ch.sj >= 0 ? sec_digit(dr[ch.sj * kSecNT + t]) : 0;
+        P::add(dsum, G.tab[ch.tab + ni * ch.dj + nj]);
+      }
+      for (int c = ndiag; c < nch; ++c) {
         const KSecChan ch = G.ch[c];
         const unsigned wi = dr[ch.si * kSecNT + t];
         const int ni = sec_digit(wi);
-        const int nj = ch.sj >= 0 ? sec_digit(dr[ch.sj * kSecNT + t]) : 0;
+        const int nj = sec_digit(dr[ch.sj * kSecNT + t]);   // moves span two sites
         const int ci = ni * ch.dj + nj;
         const C cf = G.tab[ch.tab + ci];
         if (!P::nz(cf)) continue;
-        if (ch.diag) {
-          P::add(dsum, cf);
-          continue;
-        }
         // rank terms of sites si..sj, target and source (sj > si)
-        long long dlt;
+        DT dlt;
         if (ch.dtab >= 0) {  // adjacent sites: one table entry
-          dlt = (long long)G.dl[ch.dtab + sec_rem(wi) * ch.rstride + ci];
+          dlt = G.dl[ch.dtab + sec_rem(wi) * ch.rstride + ci];
         } else {
           const int i = ch.si, j = ch.sj, q = ch.q;
           const int ri = sec_rem(wi);
-          dlt = Aat(i, ri, ni - q) - Aat(i, ri, ni);
+          long long d = Aat(i, ri, ni - q) - Aat(i, ri, ni);
           for (int k = i + 1; k < j; ++k) {
             const unsigned wk = dr[k * kSecNT + t];
             const int rk = sec_rem(wk), nk = sec_digit(wk);
-            dlt += Aat(k, rk + q, nk) - Aat(k, rk, nk);
+            d += Aat(k, rk + q, nk) - Aat(k, rk, nk);
           }
           const int rj = sec_rem(dr[j * kSecNT + t]);
-          dlt += Aat(j, rj + q, nj + q) - Aat(j, rj, nj);
+          d += Aat(j, rj + q, nj + q) - Aat(j, rj, nj);
+          dlt = (DT)d;
         }
-        const TX* xs = x + (F + dlt) * nvec + v0;
+        const TX* xs = x + at(Fd + dlt, v0);
         for (int v = 0; v < nv; ++v) P::fma(acc[v], cf, xs[v]);
       }
-      const TX* xo = x + F * nvec + v0;
-      typename P::TY* ys = y + F * nvec + v0;
+      const TX* xo = x + at(Fd, v0);
+      typename P::TY* ys = y + at(Fd, v0);
       for (int v = 0; v < nv; ++v) ys[v] = P::out(acc[v], dsum, xo[v]);
     }
   }
@@ -212,7 +222,7 @@ void free_sector(Plan* p) {
 // tables (also the plan export's source, so it touches no GPU).
 struct SecHost {
   long long Dsec = 0;
-  int K = 0;
+  int K = 0, ndiag = 0;
   bool wide = false, needA = false;
   std::vector<int> dims, Aoff;
   std::vector<long long> cnt, A, dl;
@@ -345,9 +355,15 @@ static int derive_sector(const Plan* p, long long Kl, SecHost& out) {
   tab.clear();
   dl.clear();
   bool needA = false;
-  for (size_t a = 0; a < hc.size(); ++a) {
-    if (gone[a]) continue;
+  // diagonal channels first (the kernel sums them in a loop of their own)
+  std::vector<size_t> order;
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t a = 0; a < hc.size(); ++a)
+      if (!gone[a] && (is_diag(hc[a]) == (pass == 0))) order.push_back(a);
+  int ndiag = 0;
+  for (size_t a : order) {
     const HC& h = hc[a];
+    if (is_diag(h)) ++ndiag;
     const int di = (int)h.T.size() / h.dj;
     KSecChan k{};
     k.tab = (int)tab.size();
@@ -382,6 +398,7 @@ static int derive_sector(const Plan* p, long long Kl, SecHost& out) {
     ch.push_back(k);
   }
   out.Dsec = Dsec;
+  out.ndiag = ndiag;
   out.K = K;
   out.wide = wide;
   out.needA = needA;
@@ -442,6 +459,7 @@ int build_sector(Plan* p) {
   S.N = N;
   S.K = h.K;
   S.nch = (int)h.ch.size();
+  S.ndiag = h.ndiag;
   S.d = (const int*)(b + o_d);
   S.cnt = (const long long*)(b + o_cnt);
   S.A = (const long long*)(b + o_A);

@@ -35,6 +35,7 @@ struct KSector {
   long long Dsec;          // retained states
   int N, K;                // sites, digit total
   int nch;                 // channels (all conserve the digit sum)
+  int ndiag;               // the first ndiag channels are diagonal
   int wide;                // rank deltas stored as int64 (else int32)
   const int* d;            // [N] local dimensions capped at K + 1 (rank-table strides)
   const long long* cnt;    // [(N + 1) * (K + 1)] cnt_k[t] at k * (K + 1) + t
