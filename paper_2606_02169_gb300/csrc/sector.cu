@@ -30,6 +30,7 @@ namespace hm {
 constexpr int kSecNT = 256;
 constexpr size_t kSecTablesMax = 96 * 1024;  // tables staged in shared memory up to this size
 constexpr size_t kSecDeltaMax = 48 * 1024;   // rank-delta tables of adjacent-site moves up to this size
+constexpr size_t kSecLongMax = 32 * 1024;    // long-move tables up to this size
 
 // Table pointers of one launch (shared-memory copies, or the global tables).
 template <class C, class DT>
@@ -41,6 +42,7 @@ struct SecTabs {
   const KSecChan* ch;
   const C* tab;
   const DT* dl;
+  const DT* lt;
 };
 
 __host__ __device__ inline size_t sec_align(size_t b) { return (b + 15) & ~size_t(15); }
@@ -48,10 +50,10 @@ __host__ __device__ inline size_t sec_align(size_t b) { return (b + 15) & ~size_
 // bytes of the staged tables (host and device agree on the layout); nA = 0
 // when no channel reads the rank tables
 __host__ __device__ inline size_t sec_tables_bytes(int N, int K, long long nA, int nch, long long ntab, size_t csize,
-                                                   long long ndl, size_t dsize) {
+                                                   long long ndl, long long nlt, size_t dsize) {
   return sec_align((size_t)N * 4) + sec_align((size_t)(N + 1) * (K + 1) * 8) + sec_align((size_t)nA * 8) +
          sec_align((size_t)N * 4) + sec_align((size_t)nch * sizeof(KSecChan)) + sec_align((size_t)ntab * csize) +
-         sec_align((size_t)ndl * dsize);
+         sec_align((size_t)ndl * dsize) + sec_align((size_t)nlt * dsize);
 }
 
 // Arithmetic of the sector kernel, as in the full-basis kernel: FP32 storage
@@ -156,6 +158,13 @@ __device__ __forceinline__ void sector_rows(const KSector& S, const SecTabs<type
         DT dlt;
         if (ch.dtab >= 0) {  // adjacent sites: one table entry
           dlt = G.dl[ch.dtab + sec_rem(wi) * ch.rstride + ci];
+        } else if (ch.dtab <= -2) {  // long move: one entry per site si..sj
+          const DT* T = G.lt + (-2 - ch.dtab);
+          dlt = 0;
+          for (int k = ch.si; k <= ch.sj; ++k) {
+            const unsigned wk = dr[k * kSecNT + t];
+            dlt += T[((k - ch.si) * K1 + sec_rem(wk)) * ch.rstride + sec_digit(wk)];
+          }
         } else {
           const int i = ch.si, j = ch.sj, q = ch.q;
           const int ri = sec_rem(wi);
@@ -182,7 +191,7 @@ __device__ __forceinline__ void sector_rows(const KSector& S, const SecTabs<type
 template <int AR, class DT, int NV, bool STAGED>
 __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const typename SecAr<AR>::TX* __restrict__ x,
                                                    typename SecAr<AR>::TY* __restrict__ y, int nvec, long long nA,
-                                                   long long ntab, long long ndl) {
+                                                   long long ntab, long long ndl, long long nlt) {
   using P = SecAr<AR>;
   using C = typename P::C;
   extern __shared__ __align__(16) unsigned char ssm[];
@@ -196,18 +205,20 @@ __global__ void __launch_bounds__(kSecNT) k_sector(const KSector S, const typena
     KSecChan* ch = (KSecChan*)(ssm + o);    o += sec_align((size_t)S.nch * sizeof(KSecChan));
     C* tab = (C*)(ssm + o);                 o += sec_align((size_t)ntab * sizeof(C));
     DT* dl = (DT*)(ssm + o);                o += sec_align((size_t)ndl * sizeof(DT));
+    DT* lt = (DT*)(ssm + o);                o += sec_align((size_t)nlt * sizeof(DT));
     for (int i = threadIdx.x; i < N; i += kSecNT) { d[i] = S.d[i]; Aoff[i] = S.Aoff[i]; }
     for (int i = threadIdx.x; i < (N + 1) * K1; i += kSecNT) cnt[i] = S.cnt[i];
     for (long long i = threadIdx.x; i < nA; i += kSecNT) A[i] = S.A[i];
     for (int i = threadIdx.x; i < S.nch; i += kSecNT) ch[i] = S.ch[i];
     for (long long i = threadIdx.x; i < ntab; i += kSecNT) tab[i] = P::tab(S)[i];
     for (long long i = threadIdx.x; i < ndl; i += kSecNT) dl[i] = ((const DT*)S.dl)[i];
+    for (long long i = threadIdx.x; i < nlt; i += kSecNT) lt[i] = ((const DT*)S.lt)[i];
     __syncthreads();
     // nA = 0: no channel reads the rank tables
-    const SecTabs<C, DT> G{d, cnt, A, Aoff, ch, tab, dl};
+    const SecTabs<C, DT> G{d, cnt, A, Aoff, ch, tab, dl, lt};
     sector_rows<AR, DT, NV>(S, G, (unsigned short*)(ssm + o), x, y, nvec);
   } else {
-    const SecTabs<C, DT> G{S.d, S.cnt, S.A, S.Aoff, S.ch, P::tab(S), (const DT*)S.dl};
+    const SecTabs<C, DT> G{S.d, S.cnt, S.A, S.Aoff, S.ch, P::tab(S), (const DT*)S.dl, (const DT*)S.lt};
     sector_rows<AR, DT, NV>(S, G, (unsigned short*)ssm, x, y, nvec);
   }
 }
@@ -225,7 +236,7 @@ struct SecHost {
   int K = 0, ndiag = 0;
   bool wide = false, needA = false;
   std::vector<int> dims, Aoff;
-  std::vector<long long> cnt, A, dl;
+  std::vector<long long> cnt, A, dl, lt;
   std::vector<KSecChan> ch;
   std::vector<double> tab;
 };
@@ -351,9 +362,11 @@ static int derive_sector(const Plan* p, long long Kl, SecHost& out) {
   std::vector<KSecChan>& ch = out.ch;
   std::vector<double>& tab = out.tab;
   std::vector<long long>& dl = out.dl;
+  std::vector<long long>& lt = out.lt;
   ch.clear();
   tab.clear();
   dl.clear();
+  lt.clear();
   bool needA = false;
   // diagonal channels first (the kernel sums them in a loop of their own)
   std::vector<size_t> order;
@@ -391,6 +404,36 @@ static int derive_sector(const Plan* p, long long Kl, SecHost& out) {
                 v = Ah(i, ri, si) - Ah(i, ri, ni) + Ah(j, rj + q, sj) - Ah(j, rj, nj);
               dl.push_back(v);
             }
+      } else if (h.sj > h.si + 1) {
+        // long move: per-site entries over sites i..j
+        const int i = h.si, j = h.sj, q = h.qi;
+        int dm = 1;
+        for (int kk = i; kk <= j; ++kk) dm = std::max(dm, dims[kk]);
+        const size_t nl = (size_t)(j - i + 1) * K1 * dm;
+        if ((lt.size() + nl) * dsize > kSecLongMax) {
+          needA = true;
+        } else {
+          k.dtab = -2 - (int)lt.size();
+          k.rstride = dm;
+          const size_t off = lt.size();
+          lt.resize(off + nl, 0);
+          for (int kk = i; kk <= j; ++kk) {
+            const int dfull = p->sites[kk].dim;
+            for (int r = 0; r <= K; ++r)
+              for (int n = 0; n < dims[kk]; ++n) {
+                long long v = 0;
+                if (kk == i) {           // target digit n, source n - q
+                  if (n - q >= 0 && n - q < dfull) v = Ah(kk, r, n - q) - Ah(kk, r, n);
+                } else if (kk < j) {     // digit kept, total left shifted by q
+                  if (r + q >= 0 && r + q <= K) v = Ah(kk, r + q, n) - Ah(kk, r, n);
+                } else {                 // target digit n, source n + q
+                  if (r + q >= 0 && r + q <= K && n + q >= 0 && n + q < dfull)
+                    v = Ah(kk, r + q, n + q) - Ah(kk, r, n);
+                }
+                lt[off + ((size_t)(kk - i) * K1 + r) * dm + n] = v;
+              }
+          }
+        }
       } else {
         needA = true;
       }
@@ -418,9 +461,11 @@ int build_sector(Plan* p) {
     tabf.push_back(hi);
     tabdf.push_back(make_float2(hi, (float)(v - (double)hi)));
   }
-  std::vector<int32_t> dl32;
-  if (!h.wide)
+  std::vector<int32_t> dl32, lt32;
+  if (!h.wide) {
     for (long long v : h.dl) dl32.push_back((int32_t)v);
+    for (long long v : h.lt) lt32.push_back((int32_t)v);
+  }
   // upload
   struct Sec { const void* src; size_t bytes; size_t off; };
   std::vector<Sec> secs;
@@ -441,6 +486,7 @@ int build_sector(Plan* p) {
   const size_t o_tabf = add(tabf.data(), tabf.size() * 4);
   const size_t o_tabdf = add(tabdf.data(), tabdf.size() * 8);
   const size_t o_dl = h.wide ? add(h.dl.data(), h.dl.size() * 8) : add(dl32.data(), dl32.size() * 4);
+  const size_t o_lt = h.wide ? add(h.lt.data(), h.lt.size() * 8) : add(lt32.data(), lt32.size() * 4);
   const size_t total = (cur + 255) & ~size_t(255);
   std::vector<unsigned char> host(total, 0);
   for (auto& sc : secs)
@@ -469,6 +515,8 @@ int build_sector(Plan* p) {
   S.tab_f = (const float*)(b + o_tabf);
   S.tab_df = (const float2*)(b + o_tabdf);
   S.dl = b + o_dl;
+  S.lt = b + o_lt;
+  S.nlt = (long long)h.lt.size();
   S.wide = h.wide ? 1 : 0;
   p->Dsec = h.Dsec;
   p->sec_nA = (long long)h.A.size();
@@ -505,6 +553,7 @@ std::string export_sector_json(const Plan* p, long long Kl, int* rc) {
   arr("cnt", h.cnt.size(), [&](size_t i) { o += std::to_string(h.cnt[i]); });
   arr("A", h.A.size(), [&](size_t i) { o += std::to_string(h.A[i]); });
   arr("dl", h.dl.size(), [&](size_t i) { o += std::to_string(h.dl[i]); });
+  arr("lt", h.lt.size(), [&](size_t i) { o += std::to_string(h.lt[i]); });
   arr("tab", h.tab.size(), [&](size_t i) { num(h.tab[i]); });
   arr("ch", h.ch.size(), [&](size_t i) {
     const KSecChan& k = h.ch[i];
@@ -521,8 +570,8 @@ static cudaError_t sector_launch(Plan* p, const void* x, void* y, long long nvec
   using P = SecAr<AR>;
   const KSector& S = p->ksec;
   const long long nA = p->sec_needA ? p->sec_nA : 0;
-  const size_t tabs =
-      sec_tables_bytes(S.N, S.K, nA, S.nch, p->sec_ntab, sizeof(typename P::C), p->sec_ndl, sizeof(DT));
+  const size_t tabs = sec_tables_bytes(S.N, S.K, nA, S.nch, p->sec_ntab, sizeof(typename P::C), p->sec_ndl,
+                                      S.nlt, sizeof(DT));
   const int staged = tabs <= kSecTablesMax;
   const size_t smem = (staged ? tabs : 0) + (size_t)S.N * kSecNT * sizeof(unsigned short);
   auto kern = staged ? (nvec == 1 ? k_sector<AR, DT, 1, true> : k_sector<AR, DT, 0, true>)
@@ -531,7 +580,7 @@ static cudaError_t sector_launch(Plan* p, const void* x, void* y, long long nvec
   const long long need = (S.Dsec + kSecNT - 1) / kSecNT;
   const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms() * 8));
   kern<<<grid, kSecNT, smem, s>>>(S, (const typename P::TX*)x, (typename P::TY*)y, (int)nvec, nA, p->sec_ntab,
-                                  p->sec_ndl);
+                                  p->sec_ndl, S.nlt);
   return cudaGetLastError();
 }
 

@@ -21,9 +21,10 @@ namespace hm {
 struct alignas(16) KSecChan {
   int tab;         // coefficient table base, entry [n_i * dj + n_j] (target digits)
   int dtab;        // rank-delta table base for a move on adjacent sites,
-                   // entry [rem_i * rstride + n_i * dj + n_j]; -1: rank update
-                   // from the rank tables
-  int rstride;     // d_i * dj
+                   // entry [rem_i * rstride + n_i * dj + n_j]; -2 - off: long
+                   // move, per-site entries at off in the long-move pool;
+                   // -1: rank update from the rank tables
+  int rstride;     // d_i * dj (long move: the per-site digit stride)
   int dj;          // d_j (1 for a single-site channel)
   int si, sj;      // sites (sj = -1: single-site)
   int q;           // n_target - n_source on site si (the opposite on sj)
@@ -46,6 +47,11 @@ struct KSector {
   const float* tab_f;
   const float2* tab_df;    // as float pairs (double-float arithmetic)
   const void* dl;          // rank-delta pool (int32 or int64 entries)
+  // moves spanning non-adjacent sites ("long" moves): the rank change is a
+  // sum over sites si..sj of per-site entries, for the channel with
+  // dtab = -2 - off at lt[off + ((k - si) * (K + 1) + rem_k) * rstride + n_k]
+  const void* lt;          // long-move pool (int32 or int64 entries)
+  long long nlt;           // its length
 };
 
 }  // namespace hm

@@ -145,6 +145,7 @@ def emulate_sector(S, x, nvec=1):
     cnt = np.asarray(S["cnt"], dtype=np.int64).reshape(N + 1, K1)
     A = np.asarray(S["A"], dtype=np.int64)
     dl = np.asarray(S["dl"], dtype=np.int64)
+    lt = np.asarray(S["lt"], dtype=np.int64)
     tab = np.asarray(S["tab"], dtype=np.float64)
     F = np.arange(Dsec, dtype=np.int64)
     r = F.copy()
@@ -183,6 +184,11 @@ def emulate_sector(S, x, nvec=1):
         ni, nj, ci = ni[rows], nj[rows], ci[rows]
         if dtab >= 0:
             dlt = dl[dtab + rem[si][rows] * rstride + ci]
+        elif dtab <= -2:                    # long move: per-site entries summed over si..sj
+            off = -2 - dtab
+            dlt = np.zeros(rows.size, dtype=np.int64)
+            for k in range(si, sj + 1):
+                dlt = dlt + lt[off + ((k - si) * K1 + rem[k][rows]) * rstride + dig[k][rows]]
         else:
             q = qi
             ri = rem[si][rows]

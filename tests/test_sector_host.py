@@ -81,22 +81,44 @@ def _ring(n, d=2, h=0.3, seed=0):
 
 def test_ring_channels_fold_fields_and_tabulate_adjacent_moves(capi):
     """Periodic ring of 12 spins-1/2 with fields: the 12 field channels fold
-    into the 12 bond-diagonal tables; the 22 moves on adjacent sites read a
-    rank-delta table, the 2 moves of the closing bond (sites 0 and 11)
-    update the rank over all sites; the result matches the oracle."""
+    into the 12 bond-diagonal tables (listed first); the 22 moves on
+    adjacent sites read a rank-delta table, the 2 moves of the closing bond
+    (sites 0 and 11) are long moves summed over all sites while a row is
+    unranked; no channel needs the rank tables; the result matches the
+    oracle."""
     sites, terms = _ring(12)
     S = _sector(capi, sites, terms, 6)
     ch = S["ch"]
     diag = [c for c in ch if c[8]]
     hops = [c for c in ch if not c[8]]
+    assert ch[:12] == diag
     assert len(diag) == 12 and all(c[5] >= 0 for c in diag)
     assert len(hops) == 24
     assert sum(c[1] >= 0 for c in hops) == 22
-    assert all(c[1] < 0 for c in hops if (c[4], c[5]) == (0, 11))
-    assert S["needA"] and not S["wide"]
+    assert all(c[1] <= -2 for c in hops if (c[4], c[5]) == (0, 11))
+    assert len(S["lt"]) == 2 * 12 * 7 * 2          # 2 moves x 12 sites x (K + 1) totals x 2 digits
+    assert not S["needA"] and not S["wide"]
     x = W.vector(S["Dsec"], 3)
     ref = oracle.sector_apply(sites, terms, 6, x)
     assert np.allclose(emulate_sector(S, x), ref, rtol=0, atol=1e-12)
+
+
+def test_long_moves_beyond_the_table_budget_use_the_rank_tables(capi):
+    """Many long moves on 16 sites: those whose per-site tables fit the
+    budget read them, the rest update the rank from the rank tables; both
+    agree with the oracle."""
+    n = 16
+    sites = [("spin", 2)] * n
+    terms = []
+    for a in range(n):
+        for b in range(a + 2, n, 3):
+            terms += [(a, "Sp", b, "Sm", 0.3 + 0.01 * (a + b)), (a, "Sm", b, "Sp", 0.3 + 0.01 * (a + b))]
+    terms += [(k, "Sz", -1, "I", 0.1 * k) for k in range(n)]
+    S = _sector(capi, sites, terms, 8)
+    hops = [c for c in S["ch"] if not c[8]]
+    assert any(c[1] <= -2 for c in hops) and any(c[1] == -1 for c in hops) and S["needA"]
+    x = W.vector(S["Dsec"], 6)
+    assert np.allclose(emulate_sector(S, x), oracle.sector_apply(sites, terms, 8, x), rtol=0, atol=1e-12)
 
 
 def test_open_chain_needs_no_rank_tables(capi):
