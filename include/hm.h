@@ -121,10 +121,11 @@ int hm_create(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_
  * per hop from the target's (no search). Every term must conserve the digit
  * sum (else HM_ERR_UNSUPPORTED); digit_total outside [0, sum_k (d_k - 1)]
  * gives HM_ERR_INVALID_ARG, above 255 HM_ERR_UNSUPPORTED. hm_apply,
- * hm_set_coefficients, hm_lanczos, hm_dim, hm_num_terms and hm_destroy
- * accept sector plans (arithmetic as in hm_apply);
- * hm_apply_ex, hm_apply_adjoint, hm_coupling_gradients_static, hm_tune and
- * batches return HM_ERR_UNSUPPORTED. */
+ * hm_set_coefficients, hm_lanczos, hm_evolve, hm_dim, hm_num_terms and
+ * hm_destroy accept sector plans (arithmetic as in hm_apply);
+ * hm_apply_adjoint gives gx = H^T gy = H gy for a symmetric term list (no
+ * gcoef); hm_apply_ex, hm_coupling_gradients_static, hm_tune, batches and
+ * complex term lists return HM_ERR_UNSUPPORTED. */
 int hm_create_sector(const hm_site* sites, int32_t nsites, const hm_term* terms, int32_t nterms,
                      int64_t digit_total, hm_handle* out);
 

@@ -273,7 +273,16 @@ int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, doubl
   long long nvec = nvec_in;
   real_view(dtype, nvec);
   if (!p) { set_error("invalid handle"); return HM_ERR_INVALID_ARG; }
-  if (int rc = no_sector(p, "hm_apply_adjoint")) return rc;
+  if (p->sector) {  // sector plan: gx = H^T gy = H gy for a symmetric term list
+    if (gcoef || !p->hermitian) {
+      set_error("sector plans provide gx only, and only for a symmetric term list");
+      return HM_ERR_UNSUPPORTED;
+    }
+    if (!gx) return HM_OK;
+    int rc = check_vec_args(p, gy, gx, nvec, dtype);
+    if (rc) return rc;
+    return launch_sector(p, gy, gx, nvec, dtype, (cudaStream_t)stream);
+  }
   if (p->im) {  // complex H: gx = H^dagger gy only
     if (gcoef) {
       set_error("coupling gradients are not available for a complex H");

@@ -88,6 +88,12 @@ def test_null_arguments(lib):
     assert lib.hm_apply(None, None, None, 1, 0, None) == C.HM_ERR_INVALID_ARG
     assert lib.hm_destroy(None) == C.HM_ERR_INVALID_ARG
     assert lib.hm_dim(None) < 0
+    # complex dtypes map onto the same checks; hm_evolve validates before any device call
+    assert lib.hm_apply(None, None, None, 1, C.HM_C128, None) == C.HM_ERR_INVALID_ARG
+    assert lib.hm_evolve(None, None, None, 0.1, 10, 1, 0, C.HM_C128, None, None) == C.HM_ERR_INVALID_ARG
+    assert lib.hm_evolve(None, None, None, 0.1, 10, 1, 0, C.HM_F64, None, None) == C.HM_ERR_INVALID_ARG
+    assert lib.hm_evolve(None, None, None, float("nan"), 10, 1, 0, C.HM_C64, None, None) == C.HM_ERR_INVALID_ARG
+    assert lib.hm_evolve(None, None, None, 0.1, 0, 1, 0, C.HM_C64, None, None) == C.HM_ERR_INVALID_ARG
 
 
 def test_product_path_has_no_fallback(tmp_path):

@@ -178,9 +178,20 @@ def test_sector_errors():
     assert e.value.code == C.HM_ERR_INVALID_ARG
     h = _ham(sites, [(0, "Sp", 1, "Sm", 1.0), (0, "Sm", 1, "Sp", 1.0)], 2)
     x = torch.zeros(h.D, dtype=torch.float64, device="cuda")
-    for call in (lambda: h.apply_ex(x), lambda: h.adjoint(x, x), lambda: h.tune(1, torch.float64)):
+    for call in (lambda: h.apply_ex(x), lambda: h.adjoint(x, x), lambda: h.tune(1, torch.float64),
+                 lambda: _ham(sites, [(0, "Sp", 1, "Sm", 1.0)], 2).adjoint(x, want_gcoef=False)):
         with pytest.raises(HmError) as e:
             call()
         assert e.value.code == C.HM_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         h.apply(torch.zeros(16, dtype=torch.float64, device="cuda")[:7])   # wrong length
+
+
+def test_sector_adjoint_of_a_symmetric_term_list():
+    """gx = H^T gy = H gy inside the sector (no coupling gradients)."""
+    torch = torch_cuda()
+    sites, terms = _chain(10, 2, seed=3)
+    h = _ham(sites, terms, 5)
+    gy = torch.from_numpy(W.vector(h.D, 8, nvec=2)).cuda()
+    gx, g = h.adjoint(gy, want_gcoef=False)
+    assert g is None and torch.equal(gx, h.apply(gy))
