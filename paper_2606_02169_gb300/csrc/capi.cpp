@@ -405,6 +405,8 @@ int hm_destroy(hm_handle h) {
 // per (dtype, nvec), also in a process-wide cache keyed by the site
 // dimensions and channel counts. Each candidate: one untimed launch, then the
 // minimum of three event-timed launches.
+static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream);
+
 int hm_tune(hm_handle h, int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
   long long nvec = nvec_in;
@@ -414,15 +416,14 @@ int hm_tune(hm_handle h, int64_t nvec_in, hm_dtype dtype, void* stream) {
     return HM_ERR_INVALID_ARG;
   }
   if (int rc = no_sector(p, "hm_tune")) return rc;
-  if (p->im) {  // complex H: tune both real parts for the 2 * nvec columns
-    p->im->tuned.clear();
-    Plan* q = p->im;
-    p->im = nullptr;
-    int rc = hm_tune(reinterpret_cast<hm_handle>(p), nvec, dtype, stream);
-    if (rc == HM_OK) rc = hm_tune(reinterpret_cast<hm_handle>(q), nvec, dtype, stream);
-    p->im = q;
-    return rc;
-  }
+  int rc = tune_plan(p, nvec, dtype, stream);
+  // complex H: both real parts are applied to the 2 * nvec columns
+  if (rc == HM_OK && p->im) rc = tune_plan(p->im, nvec, dtype, stream);
+  return rc;
+}
+
+// Time the launch variants of one real plan for (nvec, dtype) and store the best.
+static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
   const std::string sig = tune_signature(p, dtype, nvec);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
