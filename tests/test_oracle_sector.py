@@ -63,6 +63,22 @@ def test_spin_half_sector_dimension_is_binomial(n):
         assert oracle.sector_dimension([("spin", 2)] * n, k) == math.comb(n, k)
 
 
+@pytest.mark.parametrize("dims", [[2] * 9, [3] * 6, [2, 4, 3, 2, 5]])
+def test_sector_counts_by_enumeration(dims):
+    """cnt[k][r] = number of digit tuples of sites k..N-1 summing to r, by
+    brute-force enumeration of every suffix; for spins-1/2 it is C(N-k, r)."""
+    import itertools
+    total = sum(d - 1 for d in dims)
+    cnt = oracle.sector_counts(dims, total)
+    for k in range(len(dims) + 1):
+        want = np.zeros(total + 1, dtype=np.int64)
+        for tup in itertools.product(*[range(d) for d in dims[k:]]):
+            want[sum(tup)] += 1
+        assert list(cnt[k][: total + 1]) == list(want), k
+        if all(d == 2 for d in dims):
+            assert list(want) == [math.comb(len(dims) - k, r) for r in range(total + 1)]
+
+
 def test_mixed_sector_dimensions_and_ranking_brute_force():
     rng = np.random.default_rng(0)
     for _ in range(5):
