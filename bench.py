@@ -457,7 +457,16 @@ def run_ours(args):
                                      "peak_tinst_per_s": peak_i, "frac": ipk * value * 1e9 / peak_i}
 
     if rank == 0 and ws == 1 and not args.skip_variants:
-        line["variants"] = variants(args, h, m, x, y, ms_step, stream, hbm)
+        # the extra rows never cost the headline line: a failing one is recorded
+        try:
+            line["variants"] = variants(args, h, m, x, y, ms_step, stream, hbm)
+        except Exception as e:  # noqa: BLE001
+            line["variants"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            try:
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+            except Exception:  # noqa: BLE001
+                pass
 
     if rank == 0:
         rate, rows, dt, nth = oracle_rate(m, args.cpu_seconds)
