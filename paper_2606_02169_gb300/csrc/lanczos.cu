@@ -356,11 +356,20 @@ struct Recurrence {
   // One pass of m steps from v0 (tmp[0] = |v0|, v_0 = v0 / |v0|);
   // at_step(k, v_k) is queued before the apply of step k. beta of the last
   // step is formed too when last_beta (the residual norm of the m-step space).
+  // With a basis (m vectors of n), v_k is written straight into basis + k n
+  // (the same values as in the work vectors).
   template <class F>
-  int run(const T* v0, int m, bool last_beta, F&& at_step) {
+  int run(const T* v0, int m, bool last_beta, F&& at_step, T* basis = nullptr) {
+    if (basis) {
+      vk = basis;
+      vp = nullptr;
+    } else {
+      vk = V;
+      vp = V + n;
+    }
     dot(v0, v0, tmp, 1);
     k_scale<T><<<vb, 256, 0, s>>>(vk, v0, tmp, 0.0, n);
-    cudaMemsetAsync(vp, 0, sizeof(T) * n, s);
+    if (!basis) cudaMemsetAsync(vp, 0, sizeof(T) * n, s);
     for (int k = 0; k < m; ++k) {
       int arc = at_step(k, (const T*)vk);
       if (arc) return arc;
@@ -384,7 +393,12 @@ struct Recurrence {
       if (last && !last_beta) break;
       k_finish<<<1, 256, 0, s>>>(part, rb, dbe + k, 1);
       if (last) break;
-      std::swap(vp, vk);                                      // v_{k-1} <- v_k
+      if (basis) {                                            // v_{k-1} <- v_k
+        vp = vk;
+        vk = basis + (size_t)(k + 1) * n;
+      } else {
+        std::swap(vp, vk);
+      }
       k_scale<T><<<vb, 256, 0, s>>>(vk, w, dbe + k, 0.0, n);  // v_{k+1} = w / beta_k
     }
     cudaError_t le = cudaGetLastError();
@@ -590,11 +604,7 @@ static int evolve_t(Plan* p, const T* x, T* y, double t, int m, int nsub, int fl
   const T* u = x;
   for (int j = 0; j < nsub && rc == HM_OK; ++j) {
     T* out = ((nsub - 1 - j) % 2 == 0) ? y : scratch;
-    rc = R.run(u, m, true, [&](int k, const T* vk) -> int {
-      if (!B) return HM_OK;
-      cudaError_t e = cudaMemcpyAsync(B + (size_t)k * n, vk, sizeof(T) * n, cudaMemcpyDeviceToDevice, s);
-      return e == cudaSuccess ? HM_OK : cuda_fail(e, "Krylov basis copy");
-    });
+    rc = R.run(u, m, true, [](int, const T*) -> int { return HM_OK; }, B);  // v_k stored in B
     if (rc) break;
     std::vector<double> ha, hb;
     double nu = 0.0;
