@@ -368,6 +368,10 @@ int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int6
   }
   if (dtype != HM_F64 && dtype != HM_F32) { set_error("bad dtype"); return HM_ERR_INVALID_ARG; }
   for (size_t i = 0; i < b->members.size(); ++i) {
+    if (b->members[i]->im) {  // a coefficient update made the member complex
+      set_error("batch member " + std::to_string(i) + " has imaginary matrix elements; batches hold real plans");
+      return HM_ERR_UNSUPPORTED;
+    }
     int rc = check_vec_args(b->members[i], xs[i], ys[i], nvec, dtype);
     if (rc) {
       set_error("batch member " + std::to_string(i) + ": " + std::string(hm_last_error()));
