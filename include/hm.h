@@ -242,10 +242,12 @@ int hm_evolve(hm_handle h, const void* x, void* y, double t, int32_t m, int32_t 
               hm_dtype dtype, double* err, void* stream);
 
 /* Host only (no GPU): the coefficients hm_evolve combines a Krylov basis
- * with, c[k] = nu [exp(-i tau T) e_1]_k for k < m as (re, im) pairs in
- * c[2m], T the real symmetric tridiagonal matrix with diagonal alpha[m] and
- * off-diagonal beta[m-1] (beta may be NULL for m = 1). 1 <= m <= 128;
- * non-finite input gives HM_ERR_INVALID_ARG. */
+ * with (the propagation step of the Sec. VII use case, short-iterative
+ * Lanczos), c[k] = nu [exp(-i tau T) e_1]_k for k < m as (re, im) pairs in
+ * c[2m] (caller-owned host array), T the real symmetric tridiagonal matrix
+ * with diagonal alpha[m] and off-diagonal beta[m-1] (host arrays; beta may
+ * be NULL for m = 1). 1 <= m <= 128; non-finite input gives
+ * HM_ERR_INVALID_ARG. Synchronous, thread-safe. */
 int hm_krylov_coefficients(const double* alpha, const double* beta, int32_t m, double tau, double nu,
                            double* c);
 
