@@ -14,7 +14,8 @@ Contents
   * ``lanczos``           -- plain FP64 Lanczos with full reorthogonalisation
     (Sec. I: Krylov solvers need only y = H x).
   * ``term_gradients``    -- <gy| O_t |x> per term, by applying one-term
-    Hamiltonians; ``hellmann_feynman`` -- <psi|O_t|psi>.
+    Hamiltonians (with gy = x = psi, the Hellmann-Feynman gradient
+    <psi|O_t|psi>).
   * ``evolve``            -- y = exp(-i t H) x (Sec. VII: exact propagation
     under time-dependent or repeatedly rebuilt couplings), the definition
     written out through a dense eigendecomposition of H (tiny systems).
