@@ -159,3 +159,28 @@ def test_tile_split_of_the_benchmark_shapes(capi):
     # boson last in the leaf: every high or mid spin's JC hop is a member of
     # one of two leaf-factor groups (sqrt(n_b) and sqrt(n_b + 1))
     assert T["G"] == 3
+
+
+@pytest.mark.parametrize("dims,kinds", [((2,) * 12, None), ((2, 3) * 5, None), ((5, 4, 3, 6, 2, 2), None)])
+@pytest.mark.parametrize("nvec", [1, 2])
+def test_tile_tables_of_a_complex_h(capi, dims, kinds, nvec):
+    """The tile kernel's tables of the real and imaginary parts (bit 3) of a
+    complex H give H = H_re + i H_im on complex vectors."""
+    from plan_emulator import emulate_tile
+    m = W.random_model(list(dims), kinds, nterms=16, seed=6)
+    n = len(dims)
+    terms = m.terms + [(0, "Sy", -1, "I", 0.5), (1, "Sx", n - 1, "Sy", -0.3), (n - 1, "Sy", 2, "Sz", 0.2)]
+    D = oracle.dimension(m.sites)
+    xr, xi = W.vector(D, 11, nvec=nvec), W.vector(D, 12, nvec=nvec)
+    parts = []
+    for part in (0, 8):
+        try:
+            parts.append(capi.plan_export(m.sites, terms, part | 2 | (nvec << 8)))
+        except capi.HmError as e:
+            assert e.code == capi.HM_ERR_UNSUPPORTED
+            pytest.skip("no tile form for this split")
+    Tr, Ti = parts
+    y = (emulate_tile(Tr, xr) - emulate_tile(Ti, xi)) + 1j * (emulate_tile(Tr, xi) + emulate_tile(Ti, xr))
+    ref = oracle.apply(m.sites, terms, xr + 1j * xi, nvec=nvec)
+    assert np.abs(ref.imag).max() > 0
+    assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
