@@ -51,7 +51,9 @@ class Hamiltonian:
 
     terms: iterable of (i, op_i, j, op_j, coef), j = -1 for single-site terms;
     op names as in include/hm.h ("Sz", "Sx", "Sy", "Sp", "Sm", "Sz2", "Sp2",
-    "Sm2", "N", "a", "adag", "I")."""
+    "Sm2", "N", "a", "adag", "I"). Vectors are float64 / float32 or
+    complex128 / complex64 tensors; a term list with imaginary matrix elements
+    (Sy factors) needs complex vectors."""
 
     def __init__(self, sites, terms, sector_total=None):
         """sector_total: None for the full product basis, else the fixed sum of
