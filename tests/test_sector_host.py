@@ -150,3 +150,24 @@ def test_large_sectors_store_64_bit_deltas(capi):
     delta = S["dl"][dtab + rem19 * rstride + tgt[19] * dj + tgt[20]]
     dims = [2] * 40
     assert delta == oracle.sector_rank(dims, 20, src) - oracle.sector_rank(dims, 20, tgt)
+
+
+@pytest.mark.parametrize("K", [0, 1, 3, 6])
+def test_tavis_cummings_excitation_sectors_with_capped_boson_digits(capi, K):
+    """Five spins-1/2 coupled to one boson of 9 levels (more levels than the
+    excitation number allows, so the rank tables cap the boson's digits at
+    K + 1): every spin-boson move is long except the last spin's, and the
+    tables reproduce the oracle's projection."""
+    n = 5
+    sites = [("spin", 2)] * n + [("boson", 9)]
+    b = n
+    terms = [(b, "N", -1, "I", 1.0)]
+    for i in range(n):
+        g = 0.1 + 0.03 * i
+        terms += [(i, "Sz", -1, "I", 1.0 + 0.05 * i), (i, "Sp", b, "a", g), (i, "Sm", b, "adag", g)]
+    S = _sector(capi, sites, terms, K)
+    assert S["Dsec"] == oracle.sector_dimension(sites, K)
+    assert S["d"][b] == min(9, K + 1)
+    x = W.vector(S["Dsec"], 13)
+    ref = oracle.sector_apply(sites, terms, K, x)
+    assert np.allclose(emulate_sector(S, x), ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
