@@ -1,29 +1,30 @@
 /*
  * CPU ORACLE -- test infrastructure only.
  *
- * Plain, slow, obviously-correct restatement of the target-driven matrix-free
- * matvec y = H x of "Spin Hamiltonian as Matrix-Free Linear Map" (App. A,
- * extended by App. B for higher local powers and App. C for truncated bosons).
- * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
- * call it. It shares no code, header, table or constant with the CUDA library.
+ * A deliberately plain CPU evaluation of y = H x for the mixed spin /
+ * truncated-boson Hamiltonians of "Spin Hamiltonian as Matrix-Free Linear
+ * Map". Only the tests, the smoke check and the benchmark's CPU-baseline leg
+ * may call it. It shares no code, header, table or constant with the CUDA
+ * library.
  *
- * For every target index F (a "parfor F" over rows, Sec. II):
- *   1. decode all digits n_k = floor(F / M_k) mod d_k      (Sec. III Eq. decode)
- *   2. for each term coef * op_i(site i) * op_j(site j):
- *        expand each local op into fixed-shift monomials (q, weight, kind)
- *        (Sec. IV.A: h_+ = (h_x - i h_y)/2, so Sx = (S+ + S-)/2, Sy = (S+ - S-)/2i;
- *         App. B: Sz^2 (q=0), S+^2 (q=+2), S-^2 (q=-2);
- *         App. C: boson a^dagger (q=+1, sqrt(n_src+1)), a (q=-1, sqrt(n_src)))
- *        for every pair of monomials:
- *          source digits n_src = n - q                    (Sec. IV.B Eq. src_digit_two_site)
- *          reject if a source digit leaves [0, d-1]        (Sec. IV.B bounds)
- *          I = F - q_i M_i - q_j M_j                        (Sec. IV.B Eq. sourceoffset)
- *          y_F += coef w_i w_j c_i(n_src_i) c_j(n_src_j) x_I  (Sec. IV.B compact update)
- *      with the local coefficient evaluated on the reconstructed source
- *      projection m_src = n_src - s (App. A Lambda, App. B C^(2)_+-).
- *   3. store y_F.
+ * What it computes, row by row. The output element of basis index F is the
+ * matrix row <F|H| contracted with x. The row's local digits come from the
+ * mixed-radix place values M_k (Sec. III, Eq. decode). Each named local
+ * operator is written as a short sum of matrix elements that move the digit
+ * by a fixed amount q: 0 for Sz, Sz^2, N; +1/-1 for the spin ladders and the
+ * boson creation/annihilation operators; +2/-2 for the squared ladders.
+ * Sx and Sy are the ladder combinations of Sec. IV.A. The squared ladders
+ * and Sz^2 are App. B; a, a^dagger and N are App. C. A term that pairs two
+ * sites contributes only when both source digits stay inside their ranges.
+ * Its source index differs from F by the two moves times their place
+ * values (Sec. IV.B, Eq. sourceoffset). Its weight is the coefficient times
+ * the two local matrix elements, evaluated at the source projection
+ * (App. A ladder factors Lambda, App. B squared-ladder factors). Each row is
+ * written once.
+ *
  * Arithmetic is complex double throughout; indices are int64 with plain
- * division (no magic numbers, no tiling, no reordering).
+ * division (no magic numbers, no tiling, no reordering). Rows may be spread
+ * over OpenMP threads; each row's sum is taken in term order.
  */
 #include <complex.h>
 #include <math.h>

@@ -8,6 +8,7 @@
 // (a framework's caching pool or a fixed serving budget). For them this file
 // keeps the partials in a fixed, file-scope device array instead.
 #include <algorithm>
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <string>
@@ -16,6 +17,7 @@
 
 namespace hm {
 
+int check_vec_args(const Plan* p, const void* x, const void* y, long long nvec, hm_dtype dt);
 int grad_grid(const Plan* p);
 size_t grad_smem(const Plan* p);
 int launch_term_grad(const Plan* p, const void* gy, const void* x, double* gcoef, long long nvec, hm_dtype dt,
@@ -74,6 +76,25 @@ extern "C" int hm_coupling_gradients_static(hm_handle h, const void* gy, const v
     set_error("gy, x and gcoef must be device pointers, nvec >= 1, dtype HM_F64 or HM_F32");
     return HM_ERR_INVALID_ARG;
   }
+  // the same vector checks as hm_apply_adjoint: element alignment, the nvec
+  // cap and the int64 bound on D * nvec; gy and x may be the same vector
+  int rc = check_vec_args(p, gy, x, nvec, dtype);
+  if (rc == HM_ERR_ALIAS) rc = HM_OK;
+  if (rc) return rc;
+  if ((uintptr_t)gcoef % sizeof(double)) {
+    set_error("gcoef must be aligned to 8 bytes");
+    return HM_ERR_INVALID_ARG;
+  }
+  // the plan's tables and the scratch address are per device: the call must
+  // run with the plan's device current
+  int cur = -1;
+  cudaError_t ce = cudaGetDevice(&cur);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+  if (cur != p->device) {
+    set_error("hm_coupling_gradients_static: device " + std::to_string(cur) + " is current but the plan lives on device " +
+              std::to_string(p->device));
+    return HM_ERR_INVALID_ARG;
+  }
   const long long nterms = (long long)p->terms.size();
   if (nterms == 0) return HM_OK;
   if (nterms > kStaticPartials) {
@@ -86,7 +107,7 @@ extern "C" int hm_coupling_gradients_static(hm_handle h, const void* gy, const v
     return HM_ERR_UNSUPPORTED;
   }
   double* partial = nullptr;
-  int rc = static_partials(&partial);
+  rc = static_partials(&partial);
   if (rc) return rc;
   // each CTA writes all nterms of its row before the reduction reads them,
   // so nothing in the shared array has to be cleared between calls

@@ -80,3 +80,48 @@ def test_static_scratch_rejects_term_lists_beyond_its_size():
     rc = f(h.handle, v.data_ptr(), v.data_ptr(), g.data_ptr(), 1, 0, None)
     assert rc == _capi.HM_ERR_TOO_LARGE
     assert "131072" in lib.hm_last_error().decode()
+
+
+def test_static_scratch_checks_vectors_before_any_launch():
+    """A misaligned gy, x or gcoef is refused on the host (the same checks as
+    hm_apply_adjoint), so no kernel ever sees it."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Hamiltonian, _capi
+    lib, f = _entry()
+    m = W.square_lattice_xxz(2, 3, seed=4)
+    h = Hamiltonian(m.sites, m.terms)
+    buf = torch.zeros(h.D + 1, dtype=torch.float64, device="cuda")
+    g = torch.zeros(h.nterms + 1, dtype=torch.float64, device="cuda")
+    base, gbase = buf.data_ptr(), g.data_ptr()
+    stream = torch.cuda.current_stream().cuda_stream
+    for gy, x, gc in ((base + 4, base, gbase), (base, base + 4, gbase), (base, base, gbase + 4)):
+        rc = f(h.handle, gy, x, gc, 1, 0, stream)
+        assert rc == _capi.HM_ERR_INVALID_ARG, lib.hm_last_error().decode()
+    rc = f(h.handle, base, base, gbase, 1 << 20, 0, stream)        # nvec above 2^19
+    assert rc == _capi.HM_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(g).item() == 0                     # nothing was written
+
+
+def test_static_scratch_allocates_no_device_memory():
+    """After one warm call (kernel modules loaded, scratch address looked up),
+    further calls leave the device's free memory and torch's allocator alone."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Hamiltonian
+    lib, f = _entry()
+    m = W.square_lattice_xxz(3, 4, seed=4)
+    h = Hamiltonian(m.sites, m.terms)
+    gy = torch.from_numpy(W.vector(h.D, 5)).cuda()
+    x = torch.from_numpy(W.vector(h.D, 6)).cuda()
+    out = torch.empty(h.nterms, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert f(h.handle, gy.data_ptr(), x.data_ptr(), out.data_ptr(), 1, 0, stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert f(h.handle, gy.data_ptr(), x.data_ptr(), out.data_ptr(), 1, 0, stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
