@@ -146,7 +146,21 @@ int32_t hm_num_terms(hm_handle h);
  * pairs of stream-ordered scratch from a library memory pool per device,
  * released on the same stream after the apply; the pool keeps freed memory
  * for later calls (hm_destroy hands the unused part back). Inside a stream
- * capture the scratch becomes the graph's own allocation. */
+ * capture the scratch becomes the graph's own allocation.
+ * FP64 arithmetic: by default a double-float sum on the FP32 pipe (error-free
+ * products and sums, ~2^-46 relative per product), valid while every nonzero
+ * input |x| lies in [2^-70, 2^71) and every coefficient (table entry) in
+ * [2^-30, 2^30]. The split pass checks x on the device: if any element is
+ * outside (or subnormal, Inf, NaN) the double-float launch stands down and a
+ * second launch queued behind it computes the same call in native FP64, so
+ * results keep FP64's range for every input; a plan whose coefficients leave
+ * the window always computes in native FP64.
+ * Kernel: the general kernel (block-uniform hops as coalesced gathers, hops
+ * inside the low block from a per-plan table) unless hm_tune chose another:
+ * the general kernel on a small low block, or the staged kernel (each hop's
+ * source range streamed into shared memory by bulk asynchronous copies;
+ * its bounded waits report to hm_device_status). Those two build extra
+ * tables on their first call for each nvec, which hm_tune makes. */
 int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* Diagnostic variant of hm_apply (it ignores hm_tune's choice). flags
@@ -155,11 +169,18 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
  * transformations; ~2^-46 relative); bit 1: apply H^T instead of H; bit 2:
  * register-capped general kernel (one more resident CTA per SM); bit 3: the
  * leaf-tiled kernel (HM_ERR_UNSUPPORTED if the plan has no tile form for
- * this nvec); bit 4: the general kernel; bits 8..11: rows per iteration of
- * the tile kernel (1, 2, 4) or elements per thread of the general kernel
- * (2, 3, 4, 6, 8), 0 = default, anything else HM_ERR_INVALID_ARG. Without
- * bits 3/4 the general kernel runs. ctas > 0 forces the persistent grid
- * size (0 = library default).
+ * this nvec); bit 4: the general kernel; bit 5: the staged kernel
+ * (HM_ERR_UNSUPPORTED if the plan has no staged form for this nvec); bits
+ * 8..11: rows per iteration of the tile kernel (1, 2, 4) or elements per
+ * thread of the general kernel (2, 3, 4, 6, 8), 0 = default, anything else
+ * HM_ERR_INVALID_ARG. At most one of bits 3, 4, 5; without them the general
+ * kernel runs. Bit 6 (timing diagnostic, HM_F64 without bit 0): x already
+ * holds each value as a float pair (hi, lo) with hi + lo equal to the double
+ * within 2^-46 relative; the split pass and its range check are skipped and
+ * only the double-float apply kernel runs. Bit 7 (general kernel only): use
+ * the small low block (B * nvec <= 1024 states, the staged kernel's split)
+ * whose per-plan tables stay in L1. ctas > 0 forces the persistent grid size
+ * (0 = library default).
  * Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
@@ -197,9 +218,19 @@ int hm_apply_adjoint(hm_handle h, const void* gy, const void* x, void* gx, doubl
  * with that device current: make it before any stream capture. Every call
  * shares the array, so calls that overlap on the GPU race; each call writes
  * every partial it reads, so nothing is cleared between calls. gy, x: device
- * vectors of dtype; gcoef: device, nterms doubles, overwritten. */
+ * vectors of dtype, aligned to the element size (gy == x allowed); gcoef:
+ * device, nterms doubles, 8-byte aligned, overwritten. The plan's device
+ * must be current (else HM_ERR_INVALID_ARG); the vector checks of
+ * hm_apply_adjoint apply (nvec <= 2^19, D * nvec within int64). */
 int hm_coupling_gradients_static(hm_handle h, const void* gy, const void* x, double* gcoef,
                                  int64_t nvec, hm_dtype dtype, void* stream);
+
+/* Status word of the current device's kernels (no counterpart in the paper).
+ * Synchronises the device, then *status = the bits set since the last clear:
+ * bit 0 = a bounded wait inside the staged apply kernel gave up (the CTA left
+ * its blocks unwritten; results of that call are invalid). clear != 0 resets
+ * the word. */
+int hm_device_status(int32_t* status, int32_t clear);
 
 /* Lanczos ground state (Sec. I: Krylov solvers need only y = H x).
  * v0: device start vector (D elements of dtype, need not be normalised).
@@ -253,8 +284,9 @@ int hm_krylov_coefficients(const double* alpha, const double* beta, int32_t m, d
 
 /* Batched apply over many plans of uneven size: one persistent launch per
  * 128 instances walks an (instance, block[, chunk]) work list; an instance
- * with enough work to fill the GPU by itself gets a plain apply launch
- * instead (same results as hm_apply on it). hs[n] stay owned by the caller
+ * with enough work to fill the GPU by itself gets a plain launch of the
+ * general kernel instead. Every member's y equals hm_apply_ex with the
+ * general kernel (flag bit 4) on it, bit for bit. hs[n] stay owned by the caller
  * and must outlive the batch; each call reads the members' tables as they
  * are then (a CUDA graph captured before an hm_set_coefficients on a member
  * must be captured again). xs[b], ys[b]: device pointers (arrays of n
@@ -265,20 +297,21 @@ int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int6
 
 /* Autotuner (no counterpart in the paper; a launch-shape search): time the apply
  * variants for (nvec, dtype) on scratch vectors it allocates and frees -- the
- * general kernel (elements per thread x register cap) and the tile kernel
- * (rows per iteration), then the persistent grid size for the best -- and
+ * general kernel (elements per thread x register cap, on the plan's low
+ * block and on the small one), the staged kernel and the tile kernel (rows
+ * per iteration), then the persistent grid size for the best -- and
  * cache the fastest in the plan, and in a process-wide cache keyed by the
  * site dimensions and channel counts, for hm_apply, hm_apply_adjoint (gx) and
  * hm_lanczos. Synchronous. The variants of one kernel compute the same y bit
- * for bit; the two kernels sum in different orders (both within the FP64 /
+ * for bit; the kernels sum in different orders (all within the FP64 /
  * FP32 tolerances). */
 int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* The launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
  * out[1] = elements per thread (general) or rows per iteration (tile),
- * out[2] = register-cap variant, out[3] = kernel (1 general, 2 tile)
- * (int32_t[4], host; 0 each = library default). No counterpart in the paper
- * (a diagnostic). */
+ * out[2] = bit 0 register-cap variant, bit 1 small low block (general),
+ * out[3] = kernel (1 general, 2 tile, 3 staged) (int32_t[4], host; 0 each =
+ * library default). No counterpart in the paper (a diagnostic). */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);
 
 /* Diagnostic, host only: run the host half of hm_create (validation,

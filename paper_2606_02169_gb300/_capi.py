@@ -35,7 +35,7 @@ EXPORTS = [
     "hm_create", "hm_create_sector", "hm_set_coefficients", "hm_dim", "hm_num_terms", "hm_apply", "hm_apply_ex",
     "hm_apply_adjoint", "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune",
     "hm_tuned_config", "hm_destroy", "hm_strerror", "hm_last_error", "hm_plan_export", "hm_coupling_gradients_static",
-    "hm_evolve", "hm_krylov_coefficients",
+    "hm_evolve", "hm_krylov_coefficients", "hm_device_status",
 ]
 
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
     lib.hm_evolve.argtypes = [H, vp, vp, ctypes.c_double, i32, i32, i32, ctypes.c_int, dp, vp]
     lib.hm_krylov_coefficients.argtypes = [dp, dp, i32, ctypes.c_double, ctypes.c_double, dp]
     lib.hm_destroy.argtypes = [H]
+    lib.hm_device_status.argtypes = [ctypes.POINTER(i32), i32]
     lib.hm_plan_export.argtypes = [ctypes.POINTER(hm_site), i32, ctypes.POINTER(hm_term), i32, i32,
                                    ctypes.c_char_p, i64, ctypes.POINTER(i64)]
     lib.hm_plan_export.restype = ctypes.c_int
@@ -102,7 +103,7 @@ def load(path: str = LIB_PATH):
     lib.hm_last_error.restype = ctypes.c_char_p
     for name in ("hm_create", "hm_create_sector", "hm_set_coefficients", "hm_apply", "hm_apply_ex", "hm_apply_adjoint",
                  "hm_lanczos", "hm_batch_create", "hm_batch_apply", "hm_tune", "hm_tuned_config",
-                 "hm_destroy", "hm_evolve", "hm_krylov_coefficients"):
+                 "hm_destroy", "hm_evolve", "hm_krylov_coefficients", "hm_device_status"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -136,6 +137,15 @@ def plan_export(sites, terms, which=0):
     buf = ctypes.create_string_buffer(n.value)
     check(lib.hm_plan_export(cs, len(ss), ct, len(ts), which, buf, n.value, ctypes.byref(n)), "hm_plan_export")
     return json.loads(buf.value.decode())
+
+
+def device_status(clear=True):
+    """Status bits of the current device's kernels since the last clear
+    (bit 0: a bounded wait of the staged apply kernel gave up). Synchronises."""
+    lib = load()
+    v = ctypes.c_int32(0)
+    check(lib.hm_device_status(ctypes.byref(v), 1 if clear else 0), "hm_device_status")
+    return v.value
 
 
 def check(rc, where):

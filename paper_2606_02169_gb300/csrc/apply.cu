@@ -18,6 +18,8 @@ cudaError_t launch_batch_t(const std::vector<const Plan*>& members, const void* 
                            long long nvec, cudaStream_t st);
 template <int AR>
 cudaError_t launch_tile_t(const KTile& k, const void* x, void* y, cudaStream_t st, TuneCfg cfg);
+template <int AR>
+cudaError_t launch_stream_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
 
 static int g_nsm = 0;
 int num_sms() {
@@ -31,23 +33,44 @@ int num_sms() {
 }
 
 // FP64 input split into (hi, lo) float pairs: 16-byte loads and stores when
-// x is 16-byte aligned (the output buffer always is)
-__global__ void __launch_bounds__(256) k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n) {
+// x is 16-byte aligned (the output buffer always is). With range != NULL an
+// element outside the double-float window sets *range.
+__device__ __forceinline__ bool outside_df_window(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned ah = (unsigned)(b >> 32) & 0x7FFFFFFFu, l = (unsigned)b;
+  // |v| in [2^-70, 2^71) <=> the high word's magnitude bits in [953 << 20, 1094 << 20)
+  return (ah | l) != 0u && (ah - (953u << 20)) >= ((1094u - 953u) << 20);
+}
+
+__global__ void __launch_bounds__(256) k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n,
+                                                   int* range) {
   const long long n2 = n >> 1;
   const double2* __restrict__ x2 = reinterpret_cast<const double2*>(x);
   float4* __restrict__ xs4 = reinterpret_cast<float4*>(xs);
+  bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = __ldcs(x2 + i);
     const float2 a = split_f64(v.x), b = split_f64(v.y);
+    bad |= outside_df_window(v.x) | outside_df_window(v.y);
     xs4[i] = make_float4(a.x, a.y, b.x, b.y);
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) xs[n - 1] = split_f64(x[n - 1]);
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    xs[n - 1] = split_f64(x[n - 1]);
+    bad |= outside_df_window(x[n - 1]);
+  }
+  if (range && bad) atomicOr(range, 1);
 }
 
 // element-wise variant for an x that is only 8-byte aligned
-__global__ void __launch_bounds__(256) k_split_f64_scalar(const double* __restrict__ x, float2* __restrict__ xs, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    xs[i] = split_f64(__ldcs(x + i));
+__global__ void __launch_bounds__(256) k_split_f64_scalar(const double* __restrict__ x, float2* __restrict__ xs,
+                                                          long long n, int* range) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = __ldcs(x + i);
+    xs[i] = split_f64(v);
+    bad |= outside_df_window(v);
+  }
+  if (range && bad) atomicOr(range, 1);
 }
 
 // FP64 inputs are split into float pairs in per-call scratch from one
@@ -104,50 +127,95 @@ void scratch_trim() {
     if (m) cudaMemPoolTrimTo(m, 0);
 }
 
-cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
+cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s, int* range) {
   const long long grid = std::max<long long>(1, std::min<long long>((n / 2 + 255) / 256, (long long)num_sms() * 8));
   if (((uintptr_t)x % 16) == 0 && ((uintptr_t)xs % 16) == 0)
-    k_split_f64<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n);
+    k_split_f64<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n, range);
   else
-    k_split_f64_scalar<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n);
+    k_split_f64_scalar<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n, range);
   return cudaGetLastError();
 }
 
-int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out) {
-  int rc = scratch_alloc(b, (size_t)n * sizeof(float2), s);
+cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) { return split_into(x, xs, n, s, nullptr); }
+
+int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out, const int** range) {
+  const size_t pairs = ((size_t)n * sizeof(float2) + 255) & ~size_t(255);
+  int rc = scratch_alloc(b, pairs + (range ? 256 : 0), s);
   if (rc) return rc;
-  cudaError_t e = split_into(x, b.ptr, n, s);
+  int* flag = nullptr;
+  if (range) {
+    flag = (int*)((char*)b.ptr + pairs);
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 range flag");
+    *range = flag;
+  }
+  cudaError_t e = split_into(x, b.ptr, n, s, flag);
   if (e != cudaSuccess) return cuda_fail(e, "FP64 split launch");
   *out = (const float2*)b.ptr;
   return HM_OK;
 }
 
-// y = H x (or H^T x) on stream s. Kernel: cfg.kern = 2 the tile kernel (an
-// autotuner candidate; on the benchmark workloads it executes about twice the
-// general kernel's instructions per state), otherwise the general kernel.
+// y = H x (or H^T x) on stream s. Kernels: cfg.kern = 0 or 1 the general
+// kernel (on the plan's low block, or with cfg.small on the small one), 2 the
+// tile kernel, 3 the staged kernel (autotuner candidates). A strict request
+// (hm_apply_ex) never falls back to another kernel.
 int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64) {
   if (p->sector) return launch_sector(p, x, y, nvec, dt, s);  // the Lanczos driver on a sector plan
   const KPlan& k = transpose ? p->kt : p->k;
+  const StreamSet* ss = cfg.kern == 3 ? get_stream(p, nvec, s) : nullptr;
+  // the general kernel on the small low block (the staged kernel's tables)
+  const bool want_small = (cfg.kern == 0 || cfg.kern == 1) && cfg.small;
+  const StreamSet* small = want_small ? get_stream(p, nvec, s) : nullptr;
+  if (want_small && !small && cfg.strict) {
+    set_error("this plan has no small-block tables for that nvec");
+    return HM_ERR_UNSUPPORTED;
+  }
+  const KPlan& kg = small ? (transpose ? small->kt : small->k) : k;
+  if (small && !small->df_ok && dt == HM_F64 && !cfg.presplit) native_f64 = true;
+  if (cfg.kern == 3 && !ss && cfg.strict) {
+    set_error("this plan has no staged form for that nvec (a site above the slot size, or tables that cannot be "
+              "built during stream capture)");
+    return HM_ERR_UNSUPPORTED;
+  }
   const KTile* tk = cfg.kern == 2 ? get_tile(p, nvec, transpose, s) : nullptr;
   if (cfg.kern == 2 && !tk && cfg.strict) {
     set_error("this plan has no tile form for that nvec (or its tables cannot be built during stream capture)");
     return HM_ERR_UNSUPPORTED;
   }
-  // a tuned tile choice whose tables are unavailable (e.g. first use inside a
+  // a tuned choice whose tables are unavailable (e.g. first use inside a
   // stream capture) runs the general kernel with its default shape
   TuneCfg gcfg = cfg;
-  if (cfg.kern == 2) gcfg = TuneCfg{};
+  if (cfg.kern == 2 || cfg.kern == 3) gcfg = TuneCfg{};
   cudaError_t e;
   const void* xin = x;
   Scratch xsb;
-  if (dt == HM_F64 && !native_f64) {
+  // FP64 storage: double-float arithmetic on the split x, unless a
+  // coefficient lies outside its window (native FP64 throughout) or an input
+  // element does (the split flags it on the device; the double-float launch
+  // then stands down and a native FP64 launch of the same apply runs)
+  if (dt == HM_F64 && !native_f64 && !cfg.presplit && (!p->df_ok || (ss && !ss->df_ok))) native_f64 = true;
+  const int* range = nullptr;
+  if (dt == HM_F64 && !native_f64 && !cfg.presplit) {
     const float2* xs = nullptr;
-    int rc = split_vector(x, p->D * nvec, s, xsb, &xs);
+    int rc = split_vector(x, vec_states(p) * nvec, s, xsb, &xs, &range);
     if (rc) return rc;
     xin = xs;
+    cfg.gate = gcfg.gate = range;
+    cfg.gate_run = gcfg.gate_run = 0;
   }
   e = cudaErrorInvalidConfiguration;
+  if (ss) {
+    const KPlan& ks = transpose ? ss->kt : ss->k;
+    if (dt == HM_F32) e = launch_stream_t<AR_F32>(ks, xin, y, nvec, s, cfg);
+    else if (native_f64) e = launch_stream_t<AR_F64>(ks, xin, y, nvec, s, cfg);
+    else e = launch_stream_t<AR_DF64>(ks, xin, y, nvec, s, cfg);
+    if (e == cudaErrorInvalidConfiguration && cfg.kern == 3 && cfg.strict) {
+      set_error("staged kernel needs more shared memory than a CTA has");
+      return HM_ERR_UNSUPPORTED;
+    }
+    if (e == cudaErrorInvalidConfiguration) gcfg = TuneCfg{};
+  }
   if (tk) {
     if (dt == HM_F32) e = launch_tile_t<AR_F32>(*tk, xin, y, s, cfg);
     else if (native_f64) e = launch_tile_t<AR_F64>(*tk, xin, y, s, cfg);
@@ -158,11 +226,20 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
     }
   }
   if (e == cudaErrorInvalidConfiguration) {
-    if (dt == HM_F32) e = launch_apply_t<AR_F32>(k, xin, y, nvec, s, gcfg);
-    else if (native_f64) e = launch_apply_t<AR_F64>(k, xin, y, nvec, s, gcfg);
-    else e = launch_apply_t<AR_DF64>(k, xin, y, nvec, s, gcfg);
+    if (dt == HM_F32) e = launch_apply_t<AR_F32>(kg, xin, y, nvec, s, gcfg);
+    else if (native_f64) e = launch_apply_t<AR_F64>(kg, xin, y, nvec, s, gcfg);
+    else e = launch_apply_t<AR_DF64>(kg, xin, y, nvec, s, gcfg);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+  if (range) {  // native FP64 fallback, runs only when the split flagged x
+    TuneCfg fb{};
+    fb.gate = range;
+    fb.gate_run = 1;
+    e = cudaErrorInvalidConfiguration;
+    if (ss) e = launch_stream_t<AR_F64>(transpose ? ss->kt : ss->k, x, y, nvec, s, fb);
+    if (e == cudaErrorInvalidConfiguration) e = launch_apply_t<AR_F64>(k, x, y, nvec, s, fb);
+    if (e != cudaSuccess) return cuda_fail(e, "apply launch (FP64 fallback)");
+  }
   return HM_OK;
 }
 
@@ -245,7 +322,12 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
   for (size_t i = 0; i < b->members.size(); ++i) {
     Plan* p = b->members[i];
     if (fills_gpu(p, nvec)) {
-      int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, tuned_cfg(p, dt, nvec), false);
+      // the general kernel, whose block code the persistent queue shares:
+      // every member's y is that kernel's, bit for bit
+      TuneCfg c = tuned_cfg(p, dt, nvec);
+      if (c.kern != 1) c = TuneCfg{};
+      c.kern = 1;
+      int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, c, false);
       if (rc) return rc;
       continue;
     }

@@ -397,7 +397,8 @@ template <int MBV> struct MinBlocks<AR_F32, MBV> { static constexpr int v = 4 + 
 template <int AR, int S, bool NV1, int MBV>
 __global__ void __launch_bounds__(kNT, MinBlocks<AR, MBV>::v)
 k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>::TY* __restrict__ y,
-        int nvec, NvDiv nvdiv) {
+        int nvec, NvDiv nvdiv, KGate gate) {
+  if (gate_closed(gate)) return;
   extern __shared__ __align__(16) unsigned char sm[];
   const Lists<AR> L = carve<AR>(sm, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
   load_descriptors<AR>(P, L);
@@ -504,7 +505,8 @@ k_batch(const __grid_constant__ BatchArgs A, int nvec, NvDiv nvdiv) {
   }
 }
 
-// FP64 input split into (hi, lo) float pairs, once per apply
-__global__ void k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n);
+// FP64 input split into (hi, lo) float pairs, once per apply (range: see
+// split_vector)
+__global__ void k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n, int* range);
 
 }  // namespace hm

@@ -50,7 +50,7 @@ int num_sms();
 
 template <int AR, int S, bool NV1, int MBV>
 static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long nvec, int nchunks, cudaStream_t st,
-                             int ctas) {
+                             int ctas, KGate gate) {
   using TX = typename Ar<AR>::TX;
   using TY = typename Ar<AR>::TY;
   const size_t smem = lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag);
@@ -68,21 +68,23 @@ static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long n
   }
   const long long items = k.nblk * nchunks;
   grid = std::max<long long>(1, std::min(grid, items));
-  k_apply<AR, S, NV1, MBV><<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec));
+  k_apply<AR, S, NV1, MBV><<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec),
+                                                               gate);
   return cudaGetLastError();
 }
 
 template <int AR, int S>
 static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
                                 cudaStream_t st, TuneCfg cfg) {
+  const KGate g{cfg.gate, cfg.gate_run};
   if constexpr (AR != AR_F64) {
     if (cfg.mb) {
-      if (nvec == 1) return launch_nv<AR, S, true, 1>(k, x, y, nvec, nchunks, st, cfg.ctas);
-      return launch_nv<AR, S, false, 1>(k, x, y, nvec, nchunks, st, cfg.ctas);
+      if (nvec == 1) return launch_nv<AR, S, true, 1>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+      return launch_nv<AR, S, false, 1>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
     }
   }
-  if (nvec == 1) return launch_nv<AR, S, true, 0>(k, x, y, nvec, nchunks, st, cfg.ctas);
-  return launch_nv<AR, S, false, 0>(k, x, y, nvec, nchunks, st, cfg.ctas);
+  if (nvec == 1) return launch_nv<AR, S, true, 0>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+  return launch_nv<AR, S, false, 0>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
 }
 
 // Elements-per-thread values the kernels are instantiated for.

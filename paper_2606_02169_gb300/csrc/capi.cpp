@@ -252,10 +252,29 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
     set_error("flags ask for both kernels");
     return HM_ERR_INVALID_ARG;
   }
-  cfg.kern = tile ? 2 : (general ? 1 : 0);
+  const bool staged = (flags & 32) != 0;
+  if (staged && (tile || general)) {
+    set_error("flags ask for more than one kernel");
+    return HM_ERR_INVALID_ARG;
+  }
+  cfg.kern = tile ? 2 : (general ? 1 : (staged ? 3 : 0));
+  cfg.presplit = (flags >> 6) & 1;
+  cfg.small = (flags >> 7) & 1;
+  if (cfg.small && (tile || staged)) {
+    set_error("flag bit 7 (small low block) applies to the general kernel only");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (cfg.presplit && (dtype != HM_F64 || (flags & 1))) {
+    set_error("flag bit 6 (pre-split input) needs HM_F64 storage and the double-float arithmetic");
+    return HM_ERR_INVALID_ARG;
+  }
   cfg.strict = 1;
   if (tile && cfg.s && cfg.s != 1 && cfg.s != 2 && cfg.s != 4) {
     set_error("tile kernel rows per iteration must be 0 (default), 1, 2 or 4");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (staged && cfg.s) {
+    set_error("the staged kernel takes no elements-per-thread setting");
     return HM_ERR_INVALID_ARG;
   }
   if (!tile && cfg.s && cfg.s != 2 && cfg.s != 3 && cfg.s != 4 && cfg.s != 6 && cfg.s != 8) {
@@ -263,6 +282,7 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
     return HM_ERR_INVALID_ARG;
   }
   if (!tile && cfg.s) cfg.kern = 1;  // an element count names the general kernel
+  if (cfg.kern == 0) cfg.kern = 1;    // no kernel bit: the general kernel
   return apply_on(p, (flags & 2) != 0, x, y, nvec, dtype, (cudaStream_t)stream, cfg, (flags & 1) != 0);
 }
 
@@ -386,6 +406,7 @@ static void destroy_plan(Plan* p) {
   p->im = nullptr;
   free_plan_device(p);
   free_tiles(p);
+  free_streams(p);
   free_sector(p);
   if (p->scratch) cudaFree(p->scratch);
   p->magic = 0;
@@ -465,6 +486,28 @@ static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
   TuneCfg best{};
   best.kern = 1;
   float tbest = time_cfg(best);
+  if (rc == HM_OK && get_stream(p, nvec, s)) {
+    for (int sh : {0, 2, 4}) {
+      for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
+        TuneCfg c;
+        c.kern = 1;
+        c.small = 1;
+        c.s = sh;
+        c.mb = mb;
+        c.strict = 1;
+        const float t = time_cfg(c);
+        if (t < tbest) { tbest = t; best = c; }
+      }
+    }
+  }
+  if (rc == HM_OK && get_stream(p, nvec, s)) {
+    TuneCfg c;
+    c.kern = 3;
+    c.strict = 1;  // time the staged kernel itself, never a fallback
+    const float t = time_cfg(c);
+    if (rc == HM_ERR_UNSUPPORTED) rc = HM_OK;
+    else if (t < tbest) { tbest = t; best = c; }
+  }
   for (int sh : {2, 3, 4, 6, 8}) {
     for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
       TuneCfg c;
@@ -510,6 +553,25 @@ static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
   return HM_OK;
 }
 
+/* Device status word; see include/hm.h. */
+int hm_device_status(int32_t* status, int32_t clear) {
+  if (!status) {
+    set_error("status must not be NULL");
+    return HM_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device status sync");
+  int v = 0;
+  for (auto f : {stream_status_f32, stream_status_df64, stream_status_f64}) {
+    int w = 0;
+    int rc = f(&w, clear != 0);
+    if (rc) return rc;
+    v |= w;
+  }
+  *status = v;
+  return HM_OK;
+}
+
 /* Launch choice hm_tune stored for (nvec, dtype); see include/hm.h. */
 int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) {
   Plan* p = as_plan(h);
@@ -522,7 +584,7 @@ int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) 
   const TuneCfg c = tuned_cfg(p, dtype, nvec);
   out[0] = c.ctas;
   out[1] = c.s;
-  out[2] = c.mb;
+  out[2] = c.mb | (c.small << 1);
   out[3] = c.kern;
   return HM_OK;
 }

@@ -22,6 +22,19 @@ namespace hm {
 
 enum { AR_F32 = 0, AR_DF64 = 1, AR_F64 = 2 };
 
+// Launch gate: a kernel runs iff flag == NULL or (*flag != 0) == run. A
+// double-float apply (run = 0) and its native FP64 fallback (run = 1) are
+// queued together; the split pass sets *flag when an input is outside the
+// double-float window, so exactly one of them does the work.
+struct KGate {
+  const int* flag;
+  int run;
+};
+
+__device__ __forceinline__ bool gate_closed(const KGate g) {
+  return g.flag != nullptr && ((__ldcg(g.flag) != 0) != (g.run != 0));
+}
+
 struct DF {  // unevaluated sum s + c
   float s, c;
 };

@@ -6,6 +6,7 @@
 
 #include <complex>
 #include <map>
+#include <set>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -17,6 +18,9 @@ namespace hm {
 
 constexpr int kMaxSites = 64;
 constexpr int kLowBlockMax = 8192;  // low-digit block size bound (tables are O(B))
+// elements (states x nvec) of one block of the staged kernel: one block of x
+// fills one shared-memory slot (8 KB in FP64 storage)
+constexpr int kStreamElems = 1024;
 constexpr int kMaxDim = 65536;      // largest local dimension accepted
 constexpr long long kMaxD = (1LL << 62) - 1;
 
@@ -175,13 +179,32 @@ struct KTile {
   const double* fs_d; const float2* fs_df; const float* fs_f;  // [fs_w * F]
 };
 
+// Kernel tables of the staged apply kernel for one nvec (H and H^T), in a
+// device allocation of their own.
+struct StreamSet {
+  bool ok = false;
+  bool df_ok = true;   // every coefficient inside the double-float window
+  KPlan k{}, kt{};
+  void* dev = nullptr;
+  size_t bytes = 0;
+};
+
 // Launch choice of the apply kernel; 0 = library default for each field.
 struct TuneCfg {
   int ctas = 0;  // persistent grid size
   int s = 0;     // elements per thread (rows of a chunk)
   int mb = 0;    // 1: register cap for one more resident CTA per SM
-  int kern = 0;  // 0: library choice, 1: general kernel, 2: tile kernel
+  int kern = 0;  // 0: library choice, 1: general kernel, 2: tile kernel, 3: staged kernel
   int strict = 0;  // 1: an explicit request (hm_apply_ex) -- no fallback
+  // launch gate (device word): the kernel runs iff (*gate != 0) == gate_run;
+  // NULL = always. Pairs a double-float launch with its native FP64 fallback.
+  const int* gate = nullptr;
+  int gate_run = 0;
+  int presplit = 0;  // 1: FP64 input already holds float pairs (diagnostic timing)
+  // general kernel: 0 = the plan's low block (B <= 8192 states), 1 = the
+  // small low block of the staged tables (B * nvec <= 1024), whose per-plan
+  // tables (ELL, diagonal, packed digits) stay in L1
+  int small = 0;
 };
 
 struct Channel {            // host-side merged channel
@@ -209,6 +232,7 @@ struct Plan {
 
   KPlan k{};    // H
   KPlan kt{};   // H^T (shares k's tables when H is symmetric)
+  bool df_ok = true;  // every coefficient inside the double-float window
   void* dev = nullptr;        // one device allocation holding every table
   size_t dev_bytes = 0;
 
@@ -249,6 +273,9 @@ struct Plan {
   };
   std::map<std::pair<long long, int>, TileSet> tiles;
 
+  // staged-kernel (and small-block) tables per nvec, built on first use
+  std::map<long long, StreamSet> streams;
+
   // autotuned launch choice per (dtype, nvec); absent = default
   std::map<std::pair<int, long long>, TuneCfg> tuned;
 
@@ -261,6 +288,10 @@ struct Plan {
 // plan.cpp
 int build_plan(Plan* p);            // (re)derive tables from sites/terms and upload
 void free_plan_device(Plan* p);
+// staged-kernel tables for nvec (NULL: no staged form, or not buildable now,
+// e.g. during stream capture; then *deferred = true)
+const StreamSet* get_stream(Plan* p, long long nvec, cudaStream_t s, bool* deferred = nullptr);
+void free_streams(Plan* p);
 
 // sector.cu
 int build_sector(Plan* p);   // sector tables from p->chH (after build_plan's host half)
@@ -306,8 +337,17 @@ struct Scratch {
 };
 int scratch_alloc(Scratch& b, size_t bytes, cudaStream_t s);
 void scratch_trim();
-// n FP64 values split into float pairs in fresh scratch `b`
-int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out);
+// n FP64 values split into float pairs in fresh scratch `b`. With range !=
+// NULL the split also zeroes and then sets *range (a word in the same
+// scratch) when some element is outside the double-float window (nonzero
+// |x| < 2^-70, |x| >= 2^71, subnormal, Inf or NaN).
+int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out,
+                 const int** range = nullptr);
+// Coefficient magnitudes the double-float arithmetic takes without loss:
+// every nonzero table entry in [2^-30, 2^30] (products with x in the split
+// window stay inside float's normal range with 46-bit accuracy).
+constexpr double kDfCoefMin = 9.313225746154785e-10;   // 2^-30
+constexpr double kDfCoefMax = 1073741824.0;            // 2^30
 // y = H x (or H^dagger x when adjoint) for nvec complex right-hand sides of a
 // complex plan, dt the real type of the (re, im) pairs
 int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
@@ -327,5 +367,9 @@ int batch_setup(Plan* b);
 int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec, hm_dtype dt,
                  cudaStream_t s);
 int num_sms();
+// status words of the staged kernel's translation units on the current device
+int stream_status_f32(int* out, bool clear);
+int stream_status_df64(int* out, bool clear);
+int stream_status_f64(int* out, bool clear);
 
 }  // namespace hm

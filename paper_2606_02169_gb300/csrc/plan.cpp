@@ -304,6 +304,7 @@ struct HostTables {
 };
 
 struct HostPlanData {
+  bool df_ok = true;   // every coefficient inside the double-float window
   std::vector<KSite> ks;
   std::vector<uint32_t> ptab;
   HostTables Hf, Ht;
@@ -567,7 +568,7 @@ int plan_check(const Plan* p) {
 
 // Host half of the plan build: every table the kernels read, for H and (when
 // H is not symmetric) H^T. No device calls.
-int derive_plan(Plan* p, HostPlanData& out) {
+int derive_plan(Plan* p, HostPlanData& out, long long cap) {
   std::vector<KSite>& ks = out.ks;
   std::vector<uint32_t>& ptab = out.ptab;
   HostTables& Hf = out.Hf;
@@ -587,15 +588,15 @@ int derive_plan(Plan* p, HostPlanData& out) {
   }
   p->D = m;
 
-  // split: trailing sites whose product stays <= kLowBlockMax form the low
-  // block (digits tabulated per low index); the rest are tile-uniform.
+  // split: trailing sites whose product stays <= cap form the low block
+  // (digits tabulated per low index); the rest are tile-uniform.
   int nlow = 0;
   long long B = 1;
   for (int k = p->N - 1; k >= 0; --k) {
-    if (B * p->sites[k].dim > kLowBlockMax && nlow > 0) break;
+    if (B * p->sites[k].dim > cap && nlow > 0) break;
     B *= p->sites[k].dim;
     ++nlow;
-    if (B > kLowBlockMax) break;  // a single large site
+    if (B > cap) break;  // a single large site
   }
   p->nlow = nlow;
   p->B = (int)B;
@@ -693,13 +694,20 @@ int derive_plan(Plan* p, HostPlanData& out) {
     tk.push_back(k);
   }
   out.nhigh = nhigh;
+  // the double-float arithmetic takes every coefficient of the pools
+  auto in_window = [](double v) { return v == 0.0 || (std::fabs(v) >= kDfCoefMin && std::fabs(v) <= kDfCoefMax); };
+  for (const HostTables* H : {&Hf, &Ht}) {
+    for (double v : H->tab) out.df_ok = out.df_ok && in_window(v);
+    for (double v : H->diag) out.df_ok = out.df_ok && in_window(v);
+    for (double v : H->ell) out.df_ok = out.df_ok && in_window(v);
+  }
   return HM_OK;
 }
 
-int build_plan(Plan* p) {
-  HostPlanData hd;
-  int rc = derive_plan(p, hd);
-  if (rc) return rc;
+// Upload the tables of `hd` (derived for p's split) into one fresh device
+// allocation and fill the kernel plans of H and H^T with pointers into it.
+static int upload_tables(const Plan* p, const HostPlanData& hd, void** dev_out, size_t* bytes_out, KPlan* kh,
+                         KPlan* kth) {
   const std::vector<KSite>& ks = hd.ks;
   const std::vector<uint32_t>& ptab = hd.ptab;
   const HostTables& Hf = hd.Hf;
@@ -777,19 +785,21 @@ int build_plan(Plan* p) {
   for (auto& sc : secs)
     if (sc.bytes) std::memcpy(host.data() + sc.off, sc.src, sc.bytes);
 
-  free_plan_device(p);
-  free_tiles(p);
-  cudaError_t e = cudaMalloc(&p->dev, total);
+  void* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, total);
   if (e != cudaSuccess) {
-    p->dev = nullptr;
     set_error(std::string("cudaMalloc of plan tables failed: ") + cudaGetErrorString(e));
     return HM_ERR_OOM;
   }
-  p->dev_bytes = total;
-  e = cudaMemcpy(p->dev, host.data(), total, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(e, "plan upload");
+  }
+  *dev_out = dev;
+  *bytes_out = total;
 
-  auto P = [&](size_t off) { return (const char*)p->dev + off; };
+  auto P = [&](size_t off) { return (const char*)dev + off; };
   auto fill = [&](KPlan& k, int s) {
     const HostTables& H = *HT[s];
     int ss = p->hermitian ? 0 : s;
@@ -826,11 +836,73 @@ int build_plan(Plan* p) {
     k.ttab_df = (const float2*)P(o_ttdf);
     k.ttab_f = (const float*)P(o_ttf);
   };
-  fill(p->k, 0);
-  fill(p->kt, 1);
+  fill(*kh, 0);
+  fill(*kth, 1);
+  return HM_OK;
+}
+
+int build_plan(Plan* p) {
+  HostPlanData hd;
+  int rc = derive_plan(p, hd, kLowBlockMax);
+  if (rc) return rc;
+  free_plan_device(p);
+  free_tiles(p);
+  free_streams(p);
+  p->df_ok = hd.df_ok;
+  rc = upload_tables(p, hd, &p->dev, &p->dev_bytes, &p->k, &p->kt);
+  if (rc) {
+    p->dev = nullptr;
+    p->dev_bytes = 0;
+    return rc;
+  }
   ++p->gen;
   if (p->sector) return build_sector(p);
   return HM_OK;
+}
+
+// Tables of the staged kernel for nvec right-hand sides: the same operator
+// with a low block of at most kStreamElems / nvec states, so that one block
+// of x fits one shared-memory slot. Built on first use, cached per nvec.
+const StreamSet* get_stream(Plan* p, long long nvec, cudaStream_t s, bool* deferred) {
+  if (deferred) *deferred = false;
+  auto it = p->streams.find(nvec);
+  if (it != p->streams.end()) return it->second.ok ? &it->second : nullptr;
+  if (p->sector || nvec < 1 || nvec > kStreamElems) return nullptr;
+  // uploading needs synchronous allocation: not inside a stream capture
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    if (deferred) *deferred = true;
+    return nullptr;
+  }
+  Plan t;
+  t.N = p->N;
+  t.sites = p->sites;
+  t.terms = p->terms;
+  t.part = p->part;
+  t.device = p->device;
+  HostPlanData hd;
+  StreamSet ss;
+  const long long cap = kStreamElems / nvec;
+  if (derive_plan(&t, hd, cap) != HM_OK || (long long)t.B * nvec > kStreamElems) {
+    p->streams[nvec] = ss;  // no staged form (a single site above the slot size)
+    return nullptr;
+  }
+  if (upload_tables(&t, hd, &ss.dev, &ss.bytes, &ss.k, &ss.kt) != HM_OK) {
+    cudaGetLastError();
+    if (deferred) *deferred = true;
+    return nullptr;  // not cached: a later call may find memory
+  }
+  ss.ok = true;
+  ss.df_ok = hd.df_ok;
+  p->streams[nvec] = ss;
+  return &p->streams[nvec];
+}
+
+void free_streams(Plan* p) {
+  for (auto& kv : p->streams)
+    if (kv.second.dev) cudaFree(kv.second.dev);
+  p->streams.clear();
 }
 
 }  // namespace hm
@@ -859,7 +931,7 @@ static void jarr(std::string& o, const char* name, const V& v, F f) {
 
 int export_plan(Plan* p, int which, std::string& o) {
   HostPlanData hd;
-  int rc = derive_plan(p, hd);
+  int rc = derive_plan(p, hd, kLowBlockMax);
   if (rc) return rc;
   if ((which & 4) && p->complex_h) {
     set_error("complex term lists (imaginary matrix elements) are not available for sector plans");

@@ -340,7 +340,8 @@ template <> struct TileMinBlocks<AR_F32> { static constexpr int v = 2; };
 template <int AR, int RS>
 __global__ void __launch_bounds__(512, TileMinBlocks<AR>::v)
 k_tile(const KTile k, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>::TY* __restrict__ y,
-       long long rows_per_cta) {
+       long long rows_per_cta, KGate gate) {
+  if (gate_closed(gate)) return;
   using C = typename Ar<AR>::C;
   extern __shared__ __align__(16) unsigned char sm[];
   const int rows_cap = k.R < kTileRowsMax ? k.R : kTileRowsMax;
@@ -409,7 +410,7 @@ k_tile(const KTile k, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>
 namespace hm {
 
 template <int AR, int RS>
-static cudaError_t tile_launch(const KTile& k, const void* x, void* y, cudaStream_t st, int ctas) {
+static cudaError_t tile_launch(const KTile& k, const void* x, void* y, cudaStream_t st, int ctas, KGate gate) {
   using TX = typename Ar<AR>::TX;
   using TY = typename Ar<AR>::TY;
   const int rows_cap = k.R < kTileRowsMax ? k.R : kTileRowsMax;
@@ -432,7 +433,7 @@ static cudaError_t tile_launch(const KTile& k, const void* x, void* y, cudaStrea
   if (grid < 1) grid = 1;
   const long long per = (total + grid - 1) / grid;
   grid = (total + per - 1) / per;
-  k_tile<AR, RS><<<(unsigned)grid, k.nt, smem, st>>>(k, (const TX*)x, (TY*)y, per);
+  k_tile<AR, RS><<<(unsigned)grid, k.nt, smem, st>>>(k, (const TX*)x, (TY*)y, per, gate);
   return cudaGetLastError();
 }
 
@@ -441,9 +442,9 @@ template <int AR>
 cudaError_t launch_tile_t(const KTile& k, const void* x, void* y, cudaStream_t st, TuneCfg cfg) {
   const int rs = cfg.s ? cfg.s : (AR == AR_F32 ? 4 : 2);
   switch (rs) {
-    case 1: return tile_launch<AR, 1>(k, x, y, st, cfg.ctas);
-    case 4: return tile_launch<AR, 4>(k, x, y, st, cfg.ctas);
-    default: return tile_launch<AR, 2>(k, x, y, st, cfg.ctas);
+    case 1: return tile_launch<AR, 1>(k, x, y, st, cfg.ctas, KGate{cfg.gate, cfg.gate_run});
+    case 4: return tile_launch<AR, 4>(k, x, y, st, cfg.ctas, KGate{cfg.gate, cfg.gate_run});
+    default: return tile_launch<AR, 2>(k, x, y, st, cfg.ctas, KGate{cfg.gate, cfg.gate_run});
   }
 }
 

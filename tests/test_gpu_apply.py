@@ -160,7 +160,7 @@ def sampled_parity(model, dtype, seed, n_random, tol):
     cfg = h.tune(1, tdt)
     x = W.torch_vector(D, seed, dtype=tdt)
     y = h.apply(x)
-    y0 = h.apply_ex(x, kernel="general" if cfg["kernel"] == 1 else "tile")
+    y0 = h.apply_ex(x, kernel={1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]], small=bool(cfg["small"]))
     torch.cuda.synchronize()
     assert torch.equal(y, y0), f"tuned launch {cfg} differs from the default launch of its kernel"
     del y0

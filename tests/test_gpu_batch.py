@@ -1,5 +1,6 @@
-"""Batched persistent apply over uneven instances vs per-instance hm_apply
-(bit-identical: the same warp-tile code) and vs the oracle."""
+"""Batched persistent apply over uneven instances vs per-instance applies of
+the general kernel (bit-identical: the same block code for queued and
+plainly launched members) and vs the oracle."""
 import numpy as np
 import pytest
 
@@ -22,7 +23,7 @@ def test_batch_equals_single_applies_and_oracle():
     ys = b.apply(xs)
     torch.cuda.synchronize()
     for i, (m, h) in enumerate(zip(models, hams)):
-        single = h.apply(xs[i])
+        single = h.apply_ex(xs[i], kernel="general")
         assert torch.equal(single, ys[i]), i
         if h.D <= 3 ** 7:
             xn = xs[i].double().cpu().numpy()
@@ -50,13 +51,14 @@ def test_batch_graph_capture():
     g.replay()
     torch.cuda.synchronize()
     for h, x, y in zip(hams, xs, ys):
-        assert torch.equal(h.apply(x), y)
+        assert torch.equal(h.apply_ex(x, kernel="general"), y)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_batch_mixing_large_and_small_instances(dtype):
     """Instances that fill the GPU alone take plain launches, the rest the
-    persistent work queue; results equal per-instance hm_apply either way."""
+    persistent work queue; results equal per-instance applies of the general
+    kernel either way."""
     torch = torch_cuda()
     from paper_2606_02169_gb300 import Batch
     from gpu_util import TOL_F64, row_scale_bound
@@ -69,7 +71,7 @@ def test_batch_mixing_large_and_small_instances(dtype):
     ys = Batch(hams).apply(xs)
     torch.cuda.synchronize()
     for i, h in enumerate(hams):
-        assert torch.equal(h.apply(xs[i]), ys[i]), i
+        assert torch.equal(h.apply_ex(xs[i], kernel="general"), ys[i]), i
     # the large instance against the oracle, every row
     xn = xs[0].double().cpu().numpy()
     ref = oracle.apply(models[0].sites, models[0].terms, xn, nvec=nvec)

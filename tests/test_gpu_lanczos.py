@@ -77,3 +77,64 @@ def test_hellmann_feynman_gradients():
         cm[t] -= eps
         fd = (Edense(cp) - Edense(cm)) / (2 * eps)
         assert abs(fd - c.grad[t].item()) < 1e-6, t
+
+
+def test_lanczos_ferrimagnet_full_size_matches_oracle():
+    """The 6.05e7-state ferrimagnetic chain: the first alpha/beta of the FP64
+    device recurrence against the FP64 oracle Lanczos on the same v0 (about a
+    minute of oracle applies on the host cores)."""
+    torch = torch_cuda()
+    m = W.ferrimagnet_chain(20)
+    D = oracle.dimension(m.sites)
+    v0 = W.vector(D, 13)
+    steps = 6
+    a_ref, b_ref, _, _ = oracle.lanczos(m.sites, m.terms, v0, steps, nthreads=oracle.max_threads())
+    h = ham(m)
+    r = h.lanczos(torch.from_numpy(v0).cuda(), steps, reorth=True)
+    assert np.allclose(r["alpha"][:steps], a_ref[:steps], rtol=1e-10, atol=1e-12), (r["alpha"], a_ref)
+    assert np.allclose(r["beta"][:steps - 1], b_ref[:steps - 1], rtol=1e-10, atol=1e-12), (r["beta"], b_ref)
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-9), (np.float32, 2e-5)])
+def test_lanczos_tavis_cummings_1e9_ground_state(dtype, tol):
+    """200 Lanczos steps on the 1.07e9-state Tavis-Cummings model (24 spins,
+    64 boson levels): E0 equals the vacuum energy -omega0 N / 2 = -12 (pinned
+    on the CPU for small N); FP32 storage keeps FP64 dots."""
+    torch = torch_cuda()
+    m = W.tavis_cummings(24, 64, seed=7)
+    h = ham(m)
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    v0 = W.torch_vector(h.D, 11, dtype=tdt)
+    r = h.lanczos(v0, 200)
+    del v0
+    torch.cuda.empty_cache()
+    assert abs(r["e0"] + 12.0) <= tol * 12.0, r["e0"]
+
+
+def test_hellmann_feynman_on_the_4x5_lattice():
+    """Config-4 lattice (D = 2^20): Lanczos E0 with Hellmann-Feynman coupling
+    gradients against central differences of the device Lanczos E0."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import lanczos_e0
+    m = W.square_lattice_xxz(4, 5, seed=4)
+    D = oracle.dimension(m.sites)
+    h = ham(m)
+    c0 = [t[4] for t in m.terms]
+    v0 = torch.from_numpy(W.vector(D, 1)).cuda()
+    c = torch.tensor(c0, dtype=torch.float64, requires_grad=True)
+    E = lanczos_e0(h, c, v0, steps=150, reorth=True)
+    E.backward()
+    grad = c.grad.clone()
+
+    def e0(cc):
+        with torch.no_grad():
+            return lanczos_e0(h, torch.tensor(cc, dtype=torch.float64), v0, steps=150, reorth=True).item()
+
+    eps = 1e-4
+    rng = np.random.default_rng(0)
+    for t in sorted(rng.choice(len(c0), size=6, replace=False)):
+        cp, cm = list(c0), list(c0)
+        cp[t] += eps
+        cm[t] -= eps
+        fd = (e0(cp) - e0(cm)) / (2 * eps)
+        assert abs(fd - grad[t].item()) < 1e-6 * max(1.0, abs(fd)), (t, fd, grad[t].item())

@@ -1,6 +1,7 @@
-"""Launch variants the autotuner chooses between (elements per thread S,
-register cap, grid size): each one matches the oracle, and all of them give
-the same y bit for bit, so tuning never changes a result."""
+"""Launch variants the autotuner chooses between (kernel, elements per thread
+S, register cap, grid size): each one matches the oracle, and all launches of
+one kernel give the same y bit for bit, so tuning never changes a result
+beyond the choice of kernel."""
 import numpy as np
 import pytest
 
@@ -39,16 +40,20 @@ def test_every_variant_matches_oracle_and_each_other(dims, kinds, dtype, nvec):
     tol = TOL_F64 if dtype == np.float64 else TOL_F32
     h = ham(m)
     xd = _to(torch, x, dtype)
-    for kernel, shapes, mbs in (("general", SHAPES, (False, True)), ("tile", TILE_ROWS, (False,))):
-        base = h.apply_ex(xd, kernel=kernel)
+    for kernel, small, shapes, mbs in (("general", False, SHAPES, (False, True)),
+                                       ("general", True, SHAPES, (False, True)),
+                                       ("tile", False, TILE_ROWS, (False,)),
+                                       ("staged", False, [0], (False,))):
+        base = h.apply_ex(xd, kernel=kernel, small=small)
         torch.cuda.synchronize()
-        check_close(base.double().cpu().numpy(), ref, scale, tol, f"{kernel} default launch")
+        check_close(base.double().cpu().numpy(), ref, scale, tol, f"{kernel} small={small} default launch")
         for s in shapes:
             for mb in mbs:
                 for ctas in (0, 7):
-                    y = h.apply_ex(xd, s=s, mb=mb, ctas=ctas, kernel=kernel)
+                    y = h.apply_ex(xd, s=s, mb=mb, ctas=ctas, kernel=kernel, small=small)
                     torch.cuda.synchronize()
-                    assert torch.equal(y, base), f"{kernel} S={s} mb={mb} ctas={ctas} differs from its default"
+                    assert torch.equal(y, base), \
+                        f"{kernel} small={small} S={s} mb={mb} ctas={ctas} differs from its default"
 
 
 def test_invalid_elements_per_thread_is_rejected():
@@ -72,11 +77,11 @@ def test_tuned_apply_matches_its_kernel(dtype):
     tdt = torch.float64 if dtype == np.float64 else torch.float32
     cfg = h.tune(1, tdt)
     assert cfg == h.tuned_config(1, tdt)
-    assert cfg["kernel"] in (1, 2) and cfg["ctas"] >= 0 and cfg["mb"] in (0, 1)
-    assert cfg["s"] in ([0] + SHAPES if cfg["kernel"] == 1 else [0] + TILE_ROWS)
+    assert cfg["kernel"] in (1, 2, 3) and cfg["ctas"] >= 0 and cfg["mb"] in (0, 1)
+    assert cfg["s"] in {1: [0] + SHAPES, 2: [0] + TILE_ROWS, 3: [0]}[cfg["kernel"]]
     y1 = h.apply(xd)
-    kernel = "general" if cfg["kernel"] == 1 else "tile"
-    y2 = h.apply_ex(xd, kernel=kernel, s=cfg["s"], mb=bool(cfg["mb"]), ctas=cfg["ctas"])
+    kernel = {1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]]
+    y2 = h.apply_ex(xd, kernel=kernel, s=cfg["s"], mb=bool(cfg["mb"]), ctas=cfg["ctas"], small=bool(cfg["small"]))
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
     # a second plan with the same signature takes the cached choice without timing

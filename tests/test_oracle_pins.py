@@ -348,3 +348,24 @@ def test_hellmann_feynman_matches_finite_differences():
         e[t] = h
         fd = (E(c0 + e) - E(c0 - e)) / (2 * h)
         assert abs(fd - g[t]) <= 1e-6
+
+
+@pytest.mark.parametrize("nspins", [3, 4, 6])
+def test_tavis_cummings_ground_state_is_the_vacuum(nspins):
+    """Tavis-Cummings with omega = omega0 = 1 and g_i ~ U[0.05, 0.15] (the
+    workload's draw): every coupling term annihilates |n=0, all spins down>,
+    so it is an eigenstate of energy -omega0 N/2; with sqrt(sum g_i^2) < 1 no
+    excitation sector reaches below it, so it is the ground state. Dense
+    diagonalisation confirms E0 = -N/2 for small N (the reading behind the
+    exact E0 = -12 of the 24-spin model), and that a coupling scaled past the
+    threshold does move the ground state below the vacuum."""
+    m = W.tavis_cummings(nspins, 16, seed=7)
+    g = np.array(m.meta["g"])
+    assert np.sqrt((g ** 2).sum()) < 1.0
+    w = np.linalg.eigvalsh(oracle.dense(m.sites, m.terms).real)
+    assert abs(w[0] + nspins / 2) < 1e-12
+    assert w[1] > -nspins / 2 + 1.0 - np.sqrt((g ** 2).sum()) - 1e-9
+    strong = [(i, oi, j, oj, c * (3.0 / np.sqrt((g ** 2).sum()) if oi in ("adag", "a") else 1.0))
+              for (i, oi, j, oj, c) in m.terms]
+    ws = np.linalg.eigvalsh(oracle.dense(m.sites, strong).real)
+    assert ws[0] < -nspins / 2 - 0.1
