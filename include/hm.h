@@ -179,8 +179,10 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
  * within 2^-46 relative; the split pass and its range check are skipped and
  * only the double-float apply kernel runs. Bit 7 (general kernel only): use
  * the small low block (B * nvec <= 1024 states, the staged kernel's split)
- * whose per-plan tables stay in L1. ctas > 0 forces the persistent grid size
- * (0 = library default).
+ * whose per-plan tables stay in L1. Bit 12 (general kernel only): prefetch
+ * each thread's gathers four hops ahead with per-thread asynchronous copies
+ * into shared memory (elements per thread 4, 6 or 8). ctas > 0 forces the
+ * persistent grid size (0 = library default).
  * Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
@@ -297,9 +299,10 @@ int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int6
 
 /* Autotuner (no counterpart in the paper; a launch-shape search): time the apply
  * variants for (nvec, dtype) on scratch vectors it allocates and frees -- the
- * general kernel (elements per thread x register cap, on the plan's low
- * block and on the small one), the staged kernel and the tile kernel (rows
- * per iteration), then the persistent grid size for the best -- and
+ * general kernel (elements per thread x register cap, with and without
+ * prefetching, on the plan's low block and on the small one), the staged
+ * kernel and the tile kernel (rows per iteration), then the persistent grid
+ * size for the best -- and
  * cache the fastest in the plan, and in a process-wide cache keyed by the
  * site dimensions and channel counts, for hm_apply, hm_apply_adjoint (gx) and
  * hm_lanczos. Synchronous. The variants of one kernel compute the same y bit
@@ -309,7 +312,8 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* The launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
  * out[1] = elements per thread (general) or rows per iteration (tile),
- * out[2] = bit 0 register-cap variant, bit 1 small low block (general),
+ * out[2] = bit 0 register-cap variant, bit 1 small low block, bit 2
+ * prefetching (general kernel),
  * out[3] = kernel (1 general, 2 tile, 3 staged) (int32_t[4], host; 0 each =
  * library default). No counterpart in the paper (a diagnostic). */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);

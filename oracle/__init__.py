@@ -83,6 +83,12 @@ def _load():
             lib.oracle_multipliers.argtypes = [ctypes.c_int, i32p, i64p]
             lib.oracle_multipliers.restype = ctypes.c_int64
             lib.oracle_max_threads.restype = ctypes.c_int
+            prob = common[:10]
+            lib.oracle_rows_hashed.argtypes = prob + [ctypes.c_uint64, ctypes.c_int, i64p, ctypes.c_int64, f64p,
+                                                      f64p, ctypes.c_int]
+            lib.oracle_rows_hashed.restype = ctypes.c_int
+            lib.oracle_hashed_values.argtypes = [ctypes.c_uint64, ctypes.c_int, i64p, ctypes.c_int64, f64p]
+            lib.oracle_hashed_values.restype = None
             _lib = lib
     return _lib
 
@@ -195,6 +201,34 @@ def rows(sites, terms, x, row_idx, coefs=None, nthreads=0):
     if rc != 0:
         raise ValueError(f"oracle_rows rejected the problem (code {rc})")
     return yre + 1j * yim
+
+
+def rows_hashed(sites, terms, seed, row_idx, f32=False, coefs=None, nthreads=0):
+    """y_F for an explicit list of target rows F with x synthesised on the
+    fly from a counter-based generator (splitmix64, see oracle.c): for
+    vectors too large to hold on the host. f32: x rounded to float (FP32
+    storage)."""
+    lib = _load()
+    P = _Packed(sites, terms, coefs)
+    r = np.ascontiguousarray(row_idx, dtype=np.int64)
+    yre = np.zeros(len(r))
+    yim = np.zeros(len(r))
+    rc = lib.oracle_rows_hashed(*P.args()[:10], ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), 1 if f32 else 0,
+                                _ptr(r, ctypes.c_int64), len(r), _ptr(yre, ctypes.c_double),
+                                _ptr(yim, ctypes.c_double), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_rows_hashed rejected the problem (code {rc})")
+    return yre + 1j * yim
+
+
+def hashed_values(seed, idx, f32=False):
+    """The oracle's synthesised x at the given indices."""
+    lib = _load()
+    r = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(len(r))
+    lib.oracle_hashed_values(ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), 1 if f32 else 0, _ptr(r, ctypes.c_int64),
+                             len(r), _ptr(out, ctypes.c_double))
+    return out
 
 
 def max_threads() -> int:
@@ -394,12 +428,21 @@ def sector_apply(sites, terms, total, x, nvec=1, coefs=None):
     return y[basis].reshape(-1)
 
 
-def sector_rows(sites, terms, total, x, rows, nvec=1):
+def sector_rows(sites, terms, total, x, rows, nvec=1, seed=None, f32=False):
     """y_F for packed target rows F, following the case-2 steps of Sec. VI /
     App. D one by one: unpack the target's digits, undo each term's local move
     (every source digit pair with a nonzero local matrix element), look the
     source up in the sector (a failed lookup contributes nothing), accumulate
-    coefficient x x[source]. Row by row in Python: a few thousand rows."""
+    coefficient x x[source]. Row by row in Python: a few thousand rows.
+    With seed given (x = None, nvec = 1), x[source] is the synthesised value
+    of the counter-based generator (hashed_values), for sectors too large to
+    hold x on the host."""
+    if seed is not None:
+        class _Synth:
+            def __getitem__(self, I):
+                return hashed_values(seed, [I], f32)[0]
+        x = None
+        xs = _Synth()
     dims = [int(d) for _, d in sites]
     cnt = sector_counts(dims, total)
     mats = {}
@@ -410,7 +453,8 @@ def sector_rows(sites, terms, total, x, rows, nvec=1):
             kind, d = sites[site]
             mats[key] = local_matrix(kind, d, op)
         return mats[key]
-    x = np.asarray(x).reshape(-1, nvec)
+    if seed is None:
+        xs = np.asarray(x).reshape(-1, nvec)
     out = np.zeros((len(rows), nvec), dtype=np.complex128)
     for o, F in enumerate(rows):
         tgt = sector_unrank(dims, total, int(F), cnt)
@@ -435,7 +479,7 @@ def sector_rows(sites, terms, total, x, rows, nvec=1):
                         src[j] = sj
                     I = sector_rank(dims, total, src, cnt)
                     if I >= 0:
-                        out[o] += c * a * b * x[I]
+                        out[o] += c * a * b * xs[I]
     return out.reshape(-1)
 
 

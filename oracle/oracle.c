@@ -27,6 +27,7 @@
  * over OpenMP threads; each row's sum is taken in term order.
  */
 #include <complex.h>
+#define I_COMPLEX_UNIT _Complex_I
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -152,9 +153,38 @@ typedef struct {
     const double* cre; const double* cim;
 } problem;
 
-/* One target row: y_F = <F|H|x> (Sec. II). x is given as real and imaginary
- * parts (xim may be NULL for a real vector). */
-static double complex row_value(const problem* P, int64_t F, const double* xre, const double* xim)
+/* Input vectors too large to hold on the host are synthesised on the fly:
+ * x_i = (splitmix64 output number i+1 from state seed) >> 11, times 2^-53,
+ * minus 1/2 (i = 0, 1, ...), splitmix64 being the
+ * published finaliser of Steele, Lea and Flood (OOPSLA 2014): add the golden
+ * gamma 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds and a final
+ * xor-shift. With f32 != 0 the value is rounded to float (an FP32-storage
+ * vector). The test inputs module implements the same generator. */
+typedef struct {
+    const double* re;  /* NULL: synthesised from seed */
+    const double* im;
+    uint64_t seed;
+    int f32;
+} xsource;
+
+static double hashed_x(uint64_t seed, int64_t idx, int f32)
+{
+    uint64_t z = seed + (uint64_t)idx * 0x9E3779B97F4A7C15ULL + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    double v = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    return f32 ? (double)(float)v : v;
+}
+
+static double complex x_at(const xsource* X, int64_t idx)
+{
+    if (!X->re) return hashed_x(X->seed, idx, X->f32);
+    return X->re[idx] + I_COMPLEX_UNIT * (X->im ? X->im[idx] : 0.0);
+}
+
+/* One target row: y_F = <F|H|x> (Sec. II). */
+static double complex row_value_x(const problem* P, int64_t F, const xsource* X)
 {
     int n[128];
     for (int k = 0; k < P->nsites; ++k) n[k] = (int)((F / P->mult[k]) % P->dims[k]);
@@ -180,12 +210,18 @@ static double complex row_value(const problem* P, int64_t F, const double* xre, 
                     cb = mono_coef(mj[b].kind, P->dims[j], sj);
                 }
                 double ca = mono_coef(mi[a].kind, P->dims[i], si);
-                double complex xv = xre[src] + I * (xim ? xim[src] : 0.0);
-                acc += coef * mi[a].w * mj[b].w * ca * cb * xv;
+                acc += coef * mi[a].w * mj[b].w * ca * cb * x_at(X, src);
             }
         }
     }
     return acc;
+}
+
+/* x given as real and imaginary parts (xim may be NULL for a real vector) */
+static double complex row_value(const problem* P, int64_t F, const double* xre, const double* xim)
+{
+    xsource X = {xre, xim, 0, 0};
+    return row_value_x(P, F, &X);
 }
 
 static int setup(problem* P, int nsites, const int* kinds, const int* dims, int nterms,
@@ -252,6 +288,37 @@ int oracle_rows(int nsites, const int* kinds, const int* dims, int nterms,
         if (yim) yim[r] = cimag(v);
     }
     return 0;
+}
+
+/* y for an explicit list of rows with x synthesised from seed (above). */
+int oracle_rows_hashed(int nsites, const int* kinds, const int* dims, int nterms,
+                       const int* ti, const int* oi, const int* tj, const int* oj,
+                       const double* cre, const double* cim, uint64_t seed, int f32,
+                       const int64_t* rows, int64_t nrows, double* yre, double* yim, int nthreads)
+{
+    problem P;
+    int rc = setup(&P, nsites, kinds, dims, nterms, ti, oi, tj, oj, cre, cim);
+    if (rc) return rc;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= P.D) return -5;
+    xsource X = {NULL, NULL, seed, f32};
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t r = 0; r < nrows; ++r) {
+        double complex v = row_value_x(&P, rows[r], &X);
+        yre[r] = creal(v);
+        if (yim) yim[r] = cimag(v);
+    }
+    return 0;
+}
+
+/* x_I of the synthesised vector for an explicit list of indices (so that the
+ * tests can pin this generator against the inputs module's). */
+void oracle_hashed_values(uint64_t seed, int f32, const int64_t* idx, int64_t n, double* out)
+{
+    for (int64_t k = 0; k < n; ++k) out[k] = hashed_x(seed, idx[k], f32);
 }
 
 int oracle_max_threads(void)

@@ -20,6 +20,8 @@ template <int AR>
 cudaError_t launch_tile_t(const KTile& k, const void* x, void* y, cudaStream_t st, TuneCfg cfg);
 template <int AR>
 cudaError_t launch_stream_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
+template <int AR>
+cudaError_t launch_apply_pf_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
 
 static int g_nsm = 0;
 int num_sms() {
@@ -222,6 +224,15 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
     else e = launch_tile_t<AR_DF64>(*tk, xin, y, s, cfg);
     if (e == cudaErrorInvalidConfiguration && cfg.strict) {
       set_error("tile kernel needs more shared memory than a CTA has");
+      return HM_ERR_UNSUPPORTED;
+    }
+  }
+  if (e == cudaErrorInvalidConfiguration && gcfg.pf) {
+    if (dt == HM_F32) e = launch_apply_pf_t<AR_F32>(kg, xin, y, nvec, s, gcfg);
+    else if (native_f64) e = launch_apply_pf_t<AR_F64>(kg, xin, y, nvec, s, gcfg);
+    else e = launch_apply_pf_t<AR_DF64>(kg, xin, y, nvec, s, gcfg);
+    if (e == cudaErrorInvalidConfiguration && cfg.strict) {
+      set_error("prefetching general kernel needs more shared memory than a CTA has");
       return HM_ERR_UNSUPPORTED;
     }
   }

@@ -23,6 +23,61 @@
 namespace hm {
 
 constexpr int kNT = 256;  // threads per CTA of the apply kernels
+
+// Per-thread asynchronous copies (cp.async) of one element from global to
+// shared memory, for the prefetching variant of the general kernel: each
+// thread copies, and later reads, only its own slots, so completion is
+// tracked per thread (commit / wait_group) with no barrier between threads.
+template <class TX>
+__device__ __forceinline__ void cp_async_elem(TX* dst, const TX* src) {
+  static_assert(sizeof(TX) == 4 || sizeof(TX) == 8, "element size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(TX) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// acc[s] += sum_{j < n} c[j] * src_j[s * kNT] with src_j = base + off[j],
+// the gathers issued PF items ahead through PF per-thread shared-memory
+// stages (slot (stage, s) of this thread at pf[(stage * S + s) * kNT]).
+// mask[s] = false skips element s (its copy and its FMA).
+template <int AR, int S, int PF>
+__device__ __forceinline__ void pf_sum(typename Ar<AR>::Acc (&acc)[S], const typename Ar<AR>::C* c,
+                                       const long long* off, int n, const typename Ar<AR>::TX* base,
+                                       const bool (&mask)[S], typename Ar<AR>::TX* pf) {
+  using A = Ar<AR>;
+  using TX = typename A::TX;
+  static_assert((PF & (PF - 1)) == 0, "PF a power of two");
+#pragma unroll
+  for (int j = 0; j < PF; ++j) {
+    if (j < n) {
+      const TX* src = base + off[j];
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (mask[s]) cp_async_elem(pf + (j * S + s) * kNT, src + s * kNT);
+    }
+    cp_async_commit();
+  }
+  for (int j = 0; j < n; ++j) {
+    cp_async_wait<PF - 1>();
+    const int st = j & (PF - 1);
+    const typename A::C cj = c[j];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (mask[s]) A::fma(acc[s], cj, pf[(st * S + s) * kNT]);
+    if (j + PF < n) {
+      const TX* src = base + off[j + PF];
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (mask[s]) cp_async_elem(pf + (st * S + s) * kNT, src + s * kNT);
+    }
+    cp_async_commit();
+  }
+}
 // bytes of x the CTAs may hold in whole-block work at once (L2 is 129 MB)
 constexpr long long kInflightMax = 48LL << 20;
 
@@ -233,11 +288,11 @@ struct NvDiv {
 // One chunk of NT*S elements starting at element `e_start` of low block blk
 // (uniforms already in L). FULL: every element of the chunk lies inside the
 // block, so no per-element bounds predicates are needed. NV1: nvec == 1.
-template <int AR, int S, bool FULL, bool NV1>
+template <int AR, int S, bool FULL, bool NV1, int PF = 0>
 __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
                                             const typename Ar<AR>::TX* __restrict__ x,
                                             typename Ar<AR>::TY* __restrict__ y, int nvec_rt, NvDiv nvdiv,
-                                            long long blk, int e_start) {
+                                            long long blk, int e_start, typename Ar<AR>::TX* pfbuf = nullptr) {
   using A = Ar<AR>;
   using TX = typename A::TX;
   using TY = typename A::TY;
@@ -293,6 +348,11 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
   // ---- hops with block-uniform coefficients (high digits only); the list
   //      holds only channels whose source digits are in range (Sec. IV.B step 3) ----
   const int nact = L.n_act[0];
+  TX* pf = pfbuf ? pfbuf + threadIdx.x : nullptr;
+  if constexpr (PF > 0) {
+    // source offsets relative to the block start: act_src - ebase
+    pf_sum<AR, S, PF>(acc, L.act_c, L.act_src, nact, x + e0, ok, pf);
+  } else {
 #pragma unroll(S >= 6 ? 2 : 4)
   for (int c = 0; c < nact; ++c) {
     const C cf = L.act_c[c];
@@ -300,6 +360,7 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
 #pragma unroll
     for (int s = 0; s < S; ++s)
       if (FULL || ok[s]) A::fma(acc[s], cf, __ldg(src + s * NT));
+  }
   }
   // ---- factorised high/low hops, grouped by their low factor ----
   for (int g = P.n_grp_diag; g < P.n_grp_diag + P.n_grp; ++g) {
@@ -315,7 +376,14 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
     const int na = L.gact_n[g];
     const C* __restrict__ gu = L.gact_u + gr.m0;
     const long long* __restrict__ gs = L.gact_src + gr.m0;
-    if (L.gact_ok[g]) {
+    if (PF > 0 && L.gact_ok[g]) {
+      pf_sum<AR, S, (PF > 0 ? PF : 1)>(ag, gu, gs, na, xb, ok, pf);
+    } else if (PF > 0) {
+      bool m[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) m[s] = (FULL || ok[s]) && A::nz(v[s]);
+      pf_sum<AR, S, (PF > 0 ? PF : 1)>(ag, gu, gs, na, xb, m, pf);
+    } else if (L.gact_ok[g]) {
       // every active member's addresses lie inside x: an inadmissible low
       // digit (v = 0) gathers a finite in-range value scaled by exactly zero
 #pragma unroll(S >= 6 ? 2 : 4)
@@ -376,12 +444,12 @@ __host__ __device__ inline ChunkPlan chunk_plan(int belems, int S) {
   return c;
 }
 
-template <int AR, int S, bool NV1>
+template <int AR, int S, bool NV1, int PF = 0>
 __device__ __forceinline__ void apply_item(const KPlan& P, const Lists<AR>& L, const typename Ar<AR>::TX* x,
                                            typename Ar<AR>::TY* y, int nvec, NvDiv nvdiv, long long blk,
-                                           const ChunkPlan& cp, int c) {
+                                           const ChunkPlan& cp, int c, typename Ar<AR>::TX* pfbuf = nullptr) {
   if (c < cp.nS) {
-    apply_chunk<AR, S, true, NV1>(P, L, x, y, nvec, nvdiv, blk, c * kNT * S);
+    apply_chunk<AR, S, true, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, c * kNT * S, pfbuf);
   } else if (c < cp.nS + cp.n1) {
     apply_chunk<AR, 1, true, NV1>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + (c - cp.nS) * kNT);
   } else {
@@ -394,13 +462,26 @@ __device__ __forceinline__ void apply_item(const KPlan& P, const Lists<AR>& L, c
 template <int AR, int MBV> struct MinBlocks { static constexpr int v = 2 + MBV; };
 template <int MBV> struct MinBlocks<AR_F32, MBV> { static constexpr int v = 4 + MBV; };
 
-template <int AR, int S, bool NV1, int MBV>
+// bytes of the per-thread prefetch stages of the PF variant, placed after
+// the block lists
+template <int AR, int S, int PF>
+__host__ __device__ constexpr size_t pf_bytes() {
+  return (size_t)PF * S * kNT * sizeof(typename Ar<AR>::TX);
+}
+
+// PF = 0: gathers as plain loads; PF > 0: each thread prefetches its gathers
+// of the full-size chunks PF items ahead with cp.async (pf_sum)
+template <int AR, int S, bool NV1, int MBV, int PF = 0>
 __global__ void __launch_bounds__(kNT, MinBlocks<AR, MBV>::v)
 k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>::TY* __restrict__ y,
         int nvec, NvDiv nvdiv, KGate gate) {
   if (gate_closed(gate)) return;
   extern __shared__ __align__(16) unsigned char sm[];
   const Lists<AR> L = carve<AR>(sm, P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp, P.n_grp_diag);
+  typename Ar<AR>::TX* pfbuf = nullptr;
+  if constexpr (PF > 0)
+    pfbuf = (typename Ar<AR>::TX*)(sm + ((lists_bytes<AR>(P.n_hh_diag + P.n_hh, P.n_mem, P.n_grp_diag + P.n_grp,
+                                                          P.n_grp_diag) + 15) & ~size_t(15)));
   load_descriptors<AR>(P, L);
   const ChunkPlan cp = chunk_plan(P.B * nvec, S);
   const int nchunks = cp.count();
@@ -418,7 +499,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
     if (2 * (P.nblk - full) >= gridDim.x) full = P.nblk;
     for (long long blk = blockIdx.x; blk < full; blk += gridDim.x) {
       eval_block<AR>(P, L, blk, nvec);
-      for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, c);
+      for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, c, pfbuf);
       __syncthreads();
     }
     const long long rest = (P.nblk - full) * nchunks;
@@ -428,7 +509,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (blk - full) * nchunks));
+      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (blk - full) * nchunks), pfbuf);
       __syncthreads();
     }
   } else {
@@ -438,7 +519,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_item<AR, S, NV1>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - blk * nchunks));
+      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - blk * nchunks), pfbuf);
       __syncthreads();
     }
   }

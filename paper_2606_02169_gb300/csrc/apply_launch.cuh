@@ -48,43 +48,45 @@ inline NvDiv make_nvdiv(long long nvec) {
 
 int num_sms();
 
-template <int AR, int S, bool NV1, int MBV>
+template <int AR, int S, bool NV1, int MBV, int PF>
 static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long nvec, int nchunks, cudaStream_t st,
                              int ctas, KGate gate) {
   using TX = typename Ar<AR>::TX;
   using TY = typename Ar<AR>::TY;
-  const size_t smem = lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag);
+  auto kern = k_apply<AR, S, NV1, MBV, PF>;
+  size_t smem = lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag);
+  if (PF > 0) smem = ((smem + 15) & ~size_t(15)) + pf_bytes<AR, S, PF>();
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static size_t attr_set = 0;
   if (smem > 48 * 1024 && smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<AR, S, NV1, MBV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
   long long grid = ctas;
   if (grid <= 0) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<AR, S, NV1, MBV>, kNT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kNT, smem);
     grid = (long long)num_sms() * std::max(1, occ);
   }
   const long long items = k.nblk * nchunks;
   grid = std::max<long long>(1, std::min(grid, items));
-  k_apply<AR, S, NV1, MBV><<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec),
-                                                               gate);
+  kern<<<(unsigned)grid, kNT, smem, st>>>(k, (const TX*)x, (TY*)y, (int)nvec, make_nvdiv(nvec), gate);
   return cudaGetLastError();
 }
 
-template <int AR, int S>
+template <int AR, int S, int PF>
 static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
                                 cudaStream_t st, TuneCfg cfg) {
   const KGate g{cfg.gate, cfg.gate_run};
   if constexpr (AR != AR_F64) {
     if (cfg.mb) {
-      if (nvec == 1) return launch_nv<AR, S, true, 1>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
-      return launch_nv<AR, S, false, 1>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+      if (nvec == 1) return launch_nv<AR, S, true, 1, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+      return launch_nv<AR, S, false, 1, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
     }
   }
-  if (nvec == 1) return launch_nv<AR, S, true, 0>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
-  return launch_nv<AR, S, false, 0>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+  if (nvec == 1) return launch_nv<AR, S, true, 0, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+  return launch_nv<AR, S, false, 0, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
 }
 
 // Elements-per-thread values the kernels are instantiated for.
@@ -95,11 +97,26 @@ cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nve
   Shape sh = pick_shape((long long)k.B * nvec);
   if (cfg.s) sh = {cfg.s, chunk_plan((int)(k.B * nvec), cfg.s).count()};
   switch (sh.s) {
-    case 8: return launch_shape<AR, 8>(k, x, y, nvec, sh.nchunks, st, cfg);
-    case 6: return launch_shape<AR, 6>(k, x, y, nvec, sh.nchunks, st, cfg);
-    case 4: return launch_shape<AR, 4>(k, x, y, nvec, sh.nchunks, st, cfg);
-    case 3: return launch_shape<AR, 3>(k, x, y, nvec, sh.nchunks, st, cfg);
-    default: return launch_shape<AR, 2>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 8: return launch_shape<AR, 8, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 6: return launch_shape<AR, 6, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 4: return launch_shape<AR, 4, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+    case 3: return launch_shape<AR, 3, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+    default: return launch_shape<AR, 2, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+  }
+}
+
+// The prefetching variant (PF = 4 stages), for 4, 6 or 8 elements per
+// thread (default: the shape pick_shape chooses, rounded to those).
+template <int AR>
+cudaError_t launch_apply_pf_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg) {
+  Shape sh = pick_shape((long long)k.B * nvec);
+  int s = cfg.s ? cfg.s : sh.s;
+  s = s >= 8 ? 8 : (s >= 6 ? 6 : 4);
+  const int nchunks = chunk_plan((int)(k.B * nvec), s).count();
+  switch (s) {
+    case 8: return launch_shape<AR, 8, 4>(k, x, y, nvec, nchunks, st, cfg);
+    case 6: return launch_shape<AR, 6, 4>(k, x, y, nvec, nchunks, st, cfg);
+    default: return launch_shape<AR, 4, 4>(k, x, y, nvec, nchunks, st, cfg);
   }
 }
 

@@ -260,8 +260,13 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
   cfg.kern = tile ? 2 : (general ? 1 : (staged ? 3 : 0));
   cfg.presplit = (flags >> 6) & 1;
   cfg.small = (flags >> 7) & 1;
-  if (cfg.small && (tile || staged)) {
-    set_error("flag bit 7 (small low block) applies to the general kernel only");
+  cfg.pf = (flags >> 12) & 1;
+  if ((cfg.small || cfg.pf) && (tile || staged)) {
+    set_error("flag bits 7 and 12 (small low block, prefetching) apply to the general kernel only");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (cfg.pf && cfg.s && cfg.s != 4 && cfg.s != 6 && cfg.s != 8) {
+    set_error("the prefetching general kernel takes 4, 6 or 8 elements per thread");
     return HM_ERR_INVALID_ARG;
   }
   if (cfg.presplit && (dtype != HM_F64 || (flags & 1))) {
@@ -486,6 +491,19 @@ static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
   TuneCfg best{};
   best.kern = 1;
   float tbest = time_cfg(best);
+  for (int sh : {4, 6, 8}) {
+    for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
+      TuneCfg c;
+      c.kern = 1;
+      c.pf = 1;
+      c.s = sh;
+      c.mb = mb;
+      c.strict = 1;
+      const float t = time_cfg(c);
+      if (rc == HM_ERR_UNSUPPORTED) { rc = HM_OK; continue; }
+      if (t < tbest) { tbest = t; best = c; }
+    }
+  }
   if (rc == HM_OK && get_stream(p, nvec, s)) {
     for (int sh : {0, 2, 4}) {
       for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
@@ -584,7 +602,7 @@ int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) 
   const TuneCfg c = tuned_cfg(p, dtype, nvec);
   out[0] = c.ctas;
   out[1] = c.s;
-  out[2] = c.mb | (c.small << 1);
+  out[2] = c.mb | (c.small << 1) | (c.pf << 2);
   out[3] = c.kern;
   return HM_OK;
 }

@@ -205,6 +205,7 @@ struct TuneCfg {
   // small low block of the staged tables (B * nvec <= 1024), whose per-plan
   // tables (ELL, diagonal, packed digits) stay in L1
   int small = 0;
+  int pf = 0;  // general kernel: 1 = prefetch its gathers with cp.async (4 stages)
 };
 
 struct Channel {            // host-side merged channel

@@ -161,6 +161,7 @@ def sampled_parity(model, dtype, seed, n_random, tol):
     x = W.torch_vector(D, seed, dtype=tdt)
     y = h.apply(x)
     y0 = h.apply_ex(x, kernel={1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]], small=bool(cfg["small"]))
+    # (the prefetching variant sums like the plain general kernel)
     torch.cuda.synchronize()
     assert torch.equal(y, y0), f"tuned launch {cfg} differs from the default launch of its kernel"
     del y0

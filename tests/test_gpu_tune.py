@@ -54,6 +54,13 @@ def test_every_variant_matches_oracle_and_each_other(dims, kinds, dtype, nvec):
                     torch.cuda.synchronize()
                     assert torch.equal(y, base), \
                         f"{kernel} small={small} S={s} mb={mb} ctas={ctas} differs from its default"
+        if kernel == "general":
+            # the prefetching variant sums in the same order: bit for bit
+            for s in (4, 6, 8):
+                for mb in mbs:
+                    y = h.apply_ex(xd, s=s, mb=mb, kernel=kernel, small=small, prefetch=True)
+                    torch.cuda.synchronize()
+                    assert torch.equal(y, base), f"prefetch small={small} S={s} mb={mb} differs"
 
 
 def test_invalid_elements_per_thread_is_rejected():
@@ -81,7 +88,8 @@ def test_tuned_apply_matches_its_kernel(dtype):
     assert cfg["s"] in {1: [0] + SHAPES, 2: [0] + TILE_ROWS, 3: [0]}[cfg["kernel"]]
     y1 = h.apply(xd)
     kernel = {1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]]
-    y2 = h.apply_ex(xd, kernel=kernel, s=cfg["s"], mb=bool(cfg["mb"]), ctas=cfg["ctas"], small=bool(cfg["small"]))
+    y2 = h.apply_ex(xd, kernel=kernel, s=cfg["s"], mb=bool(cfg["mb"]), ctas=cfg["ctas"], small=bool(cfg["small"]),
+                    prefetch=bool(cfg["prefetch"]))
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
     # a second plan with the same signature takes the cached choice without timing

@@ -369,3 +369,21 @@ def test_tavis_cummings_ground_state_is_the_vacuum(nspins):
               for (i, oi, j, oj, c) in m.terms]
     ws = np.linalg.eigvalsh(oracle.dense(m.sites, strong).real)
     assert ws[0] < -nspins / 2 - 0.1
+
+
+def test_counter_based_inputs_agree_between_oracle_and_inputs_module():
+    """The synthesised vector of the large sampled tests: the oracle's C
+    generator and the inputs module's numpy generator (both written from the
+    published splitmix64 definition) give the same values, and the oracle's
+    rows with that vector equal its rows with the same vector passed in."""
+    idx = np.concatenate([np.arange(1000), np.array([2 ** 31 - 1, 2 ** 31, 2 ** 32 + 7, 6_973_568_801])])
+    for seed in (0, 21, 2 ** 63 + 5):
+        for f32 in (False, True):
+            assert np.array_equal(oracle.hashed_values(seed, idx, f32), W.hashed_values(seed, idx, f32))
+    v = W.hashed_values(1, np.arange(100000))
+    assert abs(v.mean()) < 0.01 and v.min() >= -0.5 and v.max() < 0.5
+    m = W.random_model([3, 2, 4, 2, 3], None, nterms=20, seed=4)
+    D = oracle.dimension(m.sites)
+    x = W.hashed_values(9, np.arange(D), f32=True)
+    rows = np.arange(0, D, 7)
+    assert np.array_equal(oracle.rows_hashed(m.sites, m.terms, 9, rows, f32=True), oracle.rows(m.sites, m.terms, x, rows))

@@ -264,3 +264,55 @@ def torch_vector(D: int, seed: int, nvec: int = 1, device="cuda", dtype=None, no
     if normalize:
         x /= torch.linalg.vector_norm(x.double(), dim=0, keepdim=True).to(dtype)
     return x.reshape(-1).contiguous()
+
+
+# ---------------------------------------------------------------------------
+# Counter-based input vectors for sizes whose x cannot be held on the host:
+# x_i = (splitmix64 output number i+1 from state `seed`) >> 11, times 2^-53,
+# minus 1/2. splitmix64 is the published generator of Steele, Lea and Flood
+# (OOPSLA 2014). The oracle implements the same definition in C on its own.
+# ---------------------------------------------------------------------------
+_SM_GAMMA = 0x9E3779B97F4A7C15
+_SM_M1 = 0xBF58476D1CE4E5B9
+_SM_M2 = 0x94D049BB133111EB
+
+
+def hashed_values(seed, idx, f32=False):
+    """numpy: the synthesised x at the given indices (float64; rounded to
+    float first when f32)."""
+    i = np.asarray(idx, dtype=np.int64).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed % 2 ** 64) + (i + np.uint64(1)) * np.uint64(_SM_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_SM_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_SM_M2)
+        z = z ^ (z >> np.uint64(31))
+    v = (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 - 0.5
+    return v.astype(np.float32).astype(np.float64) if f32 else v
+
+
+def _signed64(u):
+    return u - 2 ** 64 if u >= 2 ** 63 else u
+
+
+def torch_hashed_vector(D, seed, dtype=None, device="cuda", chunk=1 << 26):
+    """torch: the synthesised x of length D built on the device in chunks
+    (int64 arithmetic wraps like uint64; shifts are made logical by masks)."""
+    import torch
+    dtype = dtype or torch.float64
+    out = torch.empty(D, dtype=dtype, device=device)
+    g, m1, m2 = (torch.tensor(_signed64(c), dtype=torch.int64, device=device) for c in (_SM_GAMMA, _SM_M1, _SM_M2))
+    sd = torch.tensor(_signed64(seed % 2 ** 64), dtype=torch.int64, device=device)
+
+    def shr(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    for a in range(0, D, chunk):
+        b = min(D, a + chunk)
+        z = sd + (torch.arange(a, b, dtype=torch.int64, device=device) + 1) * g
+        z = (z ^ shr(z, 30)) * m1
+        z = (z ^ shr(z, 27)) * m2
+        z = z ^ shr(z, 31)
+        v = shr(z, 11).to(torch.float64) * 2.0 ** -53 - 0.5
+        out[a:b] = v.to(dtype)
+        del z, v
+    return out
