@@ -459,7 +459,16 @@ def run_ours(args):
         h.apply(x, out=y)
     torch.cuda.synchronize()
     clocks.start()
+    # the timed applies sit in an NVTX range "timed" (a profiler's launch
+    # list can select exactly them: ncu --nvtx --nvtx-include "timed/")
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    try:
+        nvtx.range_push("timed")
+    except Exception:  # noqa: BLE001
+        nvtx = None
     ms = timed(lambda: h.apply(x, out=y), args.steps, 0, ws, stream)
+    if nvtx is not None:
+        nvtx.range_pop()
     clk = clocks.stop()
     ms_step = ms / args.steps
     value = ws * D / (ms_step * 1e-3) / 1e9
@@ -726,23 +735,26 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     del hl, xl, gl, yl, gx, gc
     torch.cuda.empty_cache()
 
-    # time evolution exp(-i t H) x of a complex128 vector on the headline
-    # workload: one short-iterative Lanczos step of m = 30 Krylov vectors
+    # time evolution exp(-i t H) x of a complex128 vector on the ferrimagnetic
+    # chain N = 20: one short-iterative Lanczos step of m = 30 Krylov vectors
     # (basis stored, and rebuilt by a second pass), beside the complex apply
-    xc = torch.complex(x, W.torch_vector(D, 23, dtype=torch.float64))
+    mf = W.ferrimagnet_chain(20)
+    he = Hamiltonian(mf.sites, mf.terms)
+    De = he.D
+    xc = torch.complex(W.torch_vector(De, 3, dtype=torch.float64), W.torch_vector(De, 23, dtype=torch.float64))
     xc = xc / torch.linalg.vector_norm(xc)
     yc = torch.empty_like(xc)
     if args.tune:
-        h.tune(1, torch.complex128)
+        he.tune(1, torch.complex128)
     k = 10
-    ms_capply = timed(lambda: h.apply(xc, out=yc), k, 3, 1, stream) / k
+    ms_capply = timed(lambda: he.apply(xc, out=yc), k, 3, 1, stream) / k
     mk, te = 30, 0.5
 
     def evolve_ms(recompute):
-        h.evolve(xc, te, m=mk, out=yc, recompute=recompute)     # warm-up (allocations)
+        he.evolve(xc, te, m=mk, out=yc, recompute=recompute)     # warm-up (allocations)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, est = h.evolve(xc, te, m=mk, out=yc, recompute=recompute)
+        _, est = he.evolve(xc, te, m=mk, out=yc, recompute=recompute)
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) * 1e3, est
 
@@ -750,10 +762,10 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     drift = abs(float(torch.linalg.vector_norm(yc)) - 1.0)
     ms_ev2, _ = evolve_ms(True)
     out["evolve_ferrimagnet_chain_n20_c128"] = {
-        "D": D, "t": te, "krylov_m": mk, "ms_per_step_stored_basis": ms_ev, "ms_per_step_rebuilt_basis": ms_ev2,
-        "ms_complex_apply": ms_capply, "complex_gstates_s": D / ms_capply / 1e6,
+        "D": De, "t": te, "krylov_m": mk, "ms_per_step_stored_basis": ms_ev, "ms_per_step_rebuilt_basis": ms_ev2,
+        "ms_complex_apply": ms_capply, "complex_gstates_s": De / ms_capply / 1e6,
         "apply_share_stored": mk * ms_capply / ms_ev, "error_estimate": est, "norm_drift": drift}
-    del xc, yc
+    del xc, yc, he
     torch.cuda.empty_cache()
 
     # complex H: periodic spin-1/2 chain N = 26 with a Dzyaloshinskii-Moriya

@@ -4,6 +4,7 @@
 // apply_f32.cu / apply_df64.cu / apply_f64.cu.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -37,15 +38,16 @@ int num_sms() {
 // FP64 input split into (hi, lo) float pairs: 16-byte loads and stores when
 // x is 16-byte aligned (the output buffer always is). With range != NULL an
 // element outside the double-float window sets *range.
-__device__ __forceinline__ bool outside_df_window(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned ah = (unsigned)(b >> 32) & 0x7FFFFFFFu, l = (unsigned)b;
-  // |v| in [2^-70, 2^71) <=> the high word's magnitude bits in [953 << 20, 1094 << 20)
-  return (ah | l) != 0u && (ah - (953u << 20)) >= ((1094u - 953u) << 20);
+// |v| outside [lo, hi) with v != 0 (lo, hi the bit patterns of the positive
+// window ends: for non-negative doubles the bit patterns order like the
+// values, and Inf and NaN patterns lie above every finite hi)
+__device__ __forceinline__ bool outside_df_window(double v, unsigned long long lo, unsigned long long hi) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+  return a != 0ull && (a < lo || a >= hi);
 }
 
 __global__ void __launch_bounds__(256) k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n,
-                                                   int* range) {
+                                                   int* range, unsigned long long wlo, unsigned long long whi) {
   const long long n2 = n >> 1;
   const double2* __restrict__ x2 = reinterpret_cast<const double2*>(x);
   float4* __restrict__ xs4 = reinterpret_cast<float4*>(xs);
@@ -53,24 +55,25 @@ __global__ void __launch_bounds__(256) k_split_f64(const double* __restrict__ x,
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = __ldcs(x2 + i);
     const float2 a = split_f64(v.x), b = split_f64(v.y);
-    bad |= outside_df_window(v.x) | outside_df_window(v.y);
+    bad |= outside_df_window(v.x, wlo, whi) | outside_df_window(v.y, wlo, whi);
     xs4[i] = make_float4(a.x, a.y, b.x, b.y);
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     xs[n - 1] = split_f64(x[n - 1]);
-    bad |= outside_df_window(x[n - 1]);
+    bad |= outside_df_window(x[n - 1], wlo, whi);
   }
   if (range && bad) atomicOr(range, 1);
 }
 
 // element-wise variant for an x that is only 8-byte aligned
 __global__ void __launch_bounds__(256) k_split_f64_scalar(const double* __restrict__ x, float2* __restrict__ xs,
-                                                          long long n, int* range) {
+                                                          long long n, int* range, unsigned long long wlo,
+                                                          unsigned long long whi) {
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = __ldcs(x + i);
     xs[i] = split_f64(v);
-    bad |= outside_df_window(v);
+    bad |= outside_df_window(v, wlo, whi);
   }
   if (range && bad) atomicOr(range, 1);
 }
@@ -129,18 +132,28 @@ void scratch_trim() {
     if (m) cudaMemPoolTrimTo(m, 0);
 }
 
-cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s, int* range) {
+static unsigned long long dbits(double v) {
+  unsigned long long u;
+  std::memcpy(&u, &v, 8);
+  return u;
+}
+
+cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s, int* range, double xlo, double xhi) {
   const long long grid = std::max<long long>(1, std::min<long long>((n / 2 + 255) / 256, (long long)num_sms() * 8));
+  const unsigned long long wlo = dbits(xlo), whi = dbits(xhi);
   if (((uintptr_t)x % 16) == 0 && ((uintptr_t)xs % 16) == 0)
-    k_split_f64<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n, range);
+    k_split_f64<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n, range, wlo, whi);
   else
-    k_split_f64_scalar<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n, range);
+    k_split_f64_scalar<<<(unsigned)grid, 256, 0, s>>>((const double*)x, (float2*)xs, n, range, wlo, whi);
   return cudaGetLastError();
 }
 
-cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) { return split_into(x, xs, n, s, nullptr); }
+cudaError_t split_into(const void* x, void* xs, long long n, cudaStream_t s) {
+  return split_into(x, xs, n, s, nullptr, 0.0, 0.0);
+}
 
-int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out, const int** range) {
+int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out, const int** range,
+                 double xlo, double xhi) {
   const size_t pairs = ((size_t)n * sizeof(float2) + 255) & ~size_t(255);
   int rc = scratch_alloc(b, pairs + (range ? 256 : 0), s);
   if (rc) return rc;
@@ -151,7 +164,7 @@ int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const f
     if (e != cudaSuccess) return cuda_fail(e, "FP64 range flag");
     *range = flag;
   }
-  cudaError_t e = split_into(x, b.ptr, n, s, flag);
+  cudaError_t e = split_into(x, b.ptr, n, s, flag, xlo, xhi);
   if (e != cudaSuccess) return cuda_fail(e, "FP64 split launch");
   *out = (const float2*)b.ptr;
   return HM_OK;
@@ -199,8 +212,15 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
   if (dt == HM_F64 && !native_f64 && !cfg.presplit && (!p->df_ok || (ss && !ss->df_ok))) native_f64 = true;
   const int* range = nullptr;
   if (dt == HM_F64 && !native_f64 && !cfg.presplit) {
+    // the input window of the tables this call uses (the narrower of the two)
+    double xlo = p->df_xlo, xhi = p->df_xhi;
+    for (const StreamSet* t : {ss, small})
+      if (t) {
+        xlo = std::max(xlo, t->df_xlo);
+        xhi = std::min(xhi, t->df_xhi);
+      }
     const float2* xs = nullptr;
-    int rc = split_vector(x, vec_states(p) * nvec, s, xsb, &xs, &range);
+    int rc = split_vector(x, vec_states(p) * nvec, s, xsb, &xs, &range, xlo, xhi);
     if (rc) return rc;
     xin = xs;
     cfg.gate = gcfg.gate = range;

@@ -586,8 +586,9 @@ k_batch(const __grid_constant__ BatchArgs A, int nvec, NvDiv nvdiv) {
   }
 }
 
-// FP64 input split into (hi, lo) float pairs, once per apply (range: see
-// split_vector)
-__global__ void k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n, int* range);
+// FP64 input split into (hi, lo) float pairs, once per apply (range and the
+// window bit patterns wlo, whi: see split_vector)
+__global__ void k_split_f64(const double* __restrict__ x, float2* __restrict__ xs, long long n, int* range,
+                            unsigned long long wlo, unsigned long long whi);
 
 }  // namespace hm

@@ -183,7 +183,8 @@ struct KTile {
 // device allocation of their own.
 struct StreamSet {
   bool ok = false;
-  bool df_ok = true;   // every coefficient inside the double-float window
+  bool df_ok = true;   // the double-float input window is not empty
+  double df_xlo = 0.0, df_xhi = 0.0;  // that window (see df_window)
   KPlan k{}, kt{};
   void* dev = nullptr;
   size_t bytes = 0;
@@ -233,7 +234,8 @@ struct Plan {
 
   KPlan k{};    // H
   KPlan kt{};   // H^T (shares k's tables when H is symmetric)
-  bool df_ok = true;  // every coefficient inside the double-float window
+  bool df_ok = true;  // the double-float input window is not empty
+  double df_xlo = 0.0, df_xhi = 0.0;  // that window (see df_window)
   void* dev = nullptr;        // one device allocation holding every table
   size_t dev_bytes = 0;
 
@@ -340,15 +342,13 @@ int scratch_alloc(Scratch& b, size_t bytes, cudaStream_t s);
 void scratch_trim();
 // n FP64 values split into float pairs in fresh scratch `b`. With range !=
 // NULL the split also zeroes and then sets *range (a word in the same
-// scratch) when some element is outside the double-float window (nonzero
-// |x| < 2^-70, |x| >= 2^71, subnormal, Inf or NaN).
+// scratch) when some element is outside [xlo, xhi) (zero excepted; a
+// subnormal, Inf or NaN is always outside).
 int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const float2** out,
-                 const int** range = nullptr);
-// Coefficient magnitudes the double-float arithmetic takes without loss:
-// every nonzero table entry in [2^-30, 2^30] (products with x in the split
-// window stay inside float's normal range with 46-bit accuracy).
-constexpr double kDfCoefMin = 9.313225746154785e-10;   // 2^-30
-constexpr double kDfCoefMax = 1073741824.0;            // 2^30
+                 const int** range = nullptr, double xlo = 0.0, double xhi = 0.0);
+// input window [lo, hi) of the double-float arithmetic for a plan whose
+// nonzero coefficients span [cmin, cmax] (plan.cpp)
+void df_window(double cmin, double cmax, double* lo, double* hi);
 // y = H x (or H^dagger x when adjoint) for nvec complex right-hand sides of a
 // complex plan, dt the real type of the (re, im) pairs
 int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);

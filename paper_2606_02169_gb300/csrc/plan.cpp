@@ -93,6 +93,17 @@ static std::map<int, std::vector<cplx>> diagonals(const std::vector<cplx>& mat, 
   return out;
 }
 
+// Sums of several term contributions that cancel mathematically (0.2 - 0.2
+// after rounding, S+S+ parts of SxSx and SySy) leave roundoff residues of a
+// few ulps of the largest contribution. They are set to exactly zero: the
+// matrix element is zero, and a residue of ~1e-17 would otherwise count as a
+// coefficient of that size.
+constexpr double kCancelTol = 16.0 * 2.220446049250313e-16;
+
+static inline double clean_sum(double v, double maxabs) {
+  return std::fabs(v) <= kCancelTol * maxabs ? 0.0 : v;
+}
+
 static int ilog2ceil(int d) {
   int w = 0;
   while ((1 << w) < d) ++w;
@@ -101,6 +112,7 @@ static int ilog2ceil(int d) {
 
 struct Derived {
   std::vector<Channel> ch;        // merged channels of H
+  std::vector<std::vector<double>> chmax;  // largest contribution summed into each entry
   std::vector<Channel> tch;       // per-term channels (unit coefficient)
   std::vector<int> tch_term;
   cplx constant = 0.0;            // identity terms
@@ -155,13 +167,23 @@ static int expand(const Plan* p, const std::vector<double>& coefs, Derived& out)
           for (auto& v : m.T) v *= c;
           m.parts.push_back({fa, fb});
           out.ch.push_back(m);
+          out.chmax.emplace_back(m.T.size());
+          for (size_t e = 0; e < m.T.size(); ++e) out.chmax.back()[e] = std::abs(m.T[e]);
         } else {
           Channel& m = out.ch[it->second];
-          for (size_t e = 0; e < m.T.size(); ++e) m.T[e] += c * unit.T[e];
+          for (size_t e = 0; e < m.T.size(); ++e) {
+            m.T[e] += c * unit.T[e];
+            out.chmax[it->second][e] = std::max(out.chmax[it->second][e], std::abs(c * unit.T[e]));
+          }
           m.parts.push_back({fa, fb});
         }
       }
   }
+  for (size_t c = 0; c < out.ch.size(); ++c)
+    for (size_t e = 0; e < out.ch[c].T.size(); ++e) {
+      const cplx v = out.ch[c].T[e];
+      out.ch[c].T[e] = cplx(clean_sum(v.real(), out.chmax[c][e]), clean_sum(v.imag(), out.chmax[c][e]));
+    }
   return HM_OK;
 }
 
@@ -304,7 +326,7 @@ struct HostTables {
 };
 
 struct HostPlanData {
-  bool df_ok = true;   // every coefficient inside the double-float window
+  double cmin = 0.0, cmax = 0.0;   // smallest / largest nonzero |coefficient| of the pools
   std::vector<KSite> ks;
   std::vector<uint32_t> ptab;
   HostTables Hf, Ht;
@@ -330,6 +352,7 @@ static void build_tables(const Plan* p, const std::vector<Channel>& chans, cplx 
   };
   std::vector<KChan> hh_diag, hh;
   H.diag.assign(B, constant.real());
+  std::vector<double> diagmax(B, std::fabs(constant.real()));
   auto low_digit = [&](int lo, int site) -> int {
     return (int)((ptab[lo] >> ks[site].lbit) & ((1u << ks[site].lwid) - 1u));
   };
@@ -359,7 +382,10 @@ static void build_tables(const Plan* p, const std::vector<Channel>& chans, cplx 
         int nj = (c.j >= 0) ? low_digit(lo, c.j) : 0;
         double v = c.T[(size_t)ni * c.dj + nj].real();
         if (v == 0.0) continue;
-        if (diag) H.diag[lo] += v;
+        if (diag) {
+          H.diag[lo] += v;
+          diagmax[lo] = std::max(diagmax[lo], std::fabs(v));
+        }
         else ell_rows[lo].push_back({(int)off, v});
       }
       continue;
@@ -397,10 +423,16 @@ static void build_tables(const Plan* p, const std::vector<Channel>& chans, cplx 
       // coefficient sits on the high factor
       m.v = lowf0;
       m.u.assign(dh, 0.0);
+      std::vector<double> ucontrib(dh, 0.0);
       for (auto& pr : c.parts) {
         const auto& hf = low_is_i ? pr.second : pr.first;
-        for (int n = 0; n < dh; ++n) m.u[n] += hf[n];
+        for (int n = 0; n < dh; ++n) {
+          m.u[n] += hf[n];
+          ucontrib[n] = std::max(ucontrib[n], std::abs(hf[n]));
+        }
       }
+      for (int n = 0; n < dh; ++n)
+        m.u[n] = cplx(clean_sum(m.u[n].real(), ucontrib[n]), clean_sum(m.u[n].imag(), ucontrib[n]));
       if (low_is_i) m.factored = false;  // unreachable for suffix low blocks; keep the table path
       // u and v may each be imaginary with a real product (SySy): move the
       // phase of v onto u so that both are real, else use the table path
@@ -423,6 +455,7 @@ static void build_tables(const Plan* p, const std::vector<Channel>& chans, cplx 
     }
     mixed.push_back(std::move(m));
   }
+  for (int lo = 0; lo < B; ++lo) H.diag[lo] = clean_sum(H.diag[lo], diagmax[lo]);
 
   // ---- groups ----
   std::vector<KGroup> gd, go;
@@ -488,11 +521,19 @@ static void build_tables(const Plan* p, const std::vector<Channel>& chans, cplx 
   for (auto& r : ell_rows) {
     std::sort(r.begin(), r.end(), [](auto& a, auto& b) { return a.first < b.first; });
     std::vector<std::pair<int, double>> mm;
+    std::vector<double> mx;
     for (auto& e : r) {
-      if (!mm.empty() && mm.back().first == e.first) mm.back().second += e.second;
-      else mm.push_back(e);
+      if (!mm.empty() && mm.back().first == e.first) {
+        mm.back().second += e.second;
+        mx.back() = std::max(mx.back(), std::fabs(e.second));
+      } else {
+        mm.push_back(e);
+        mx.push_back(std::fabs(e.second));
+      }
     }
-    r.swap(mm);
+    r.clear();
+    for (size_t k = 0; k < mm.size(); ++k)
+      if (clean_sum(mm[k].second, mx[k]) != 0.0) r.push_back(mm[k]);
     w = std::max(w, (int)r.size());
   }
   H.ell_w = w;
@@ -694,14 +735,39 @@ int derive_plan(Plan* p, HostPlanData& out, long long cap) {
     tk.push_back(k);
   }
   out.nhigh = nhigh;
-  // the double-float arithmetic takes every coefficient of the pools
-  auto in_window = [](double v) { return v == 0.0 || (std::fabs(v) >= kDfCoefMin && std::fabs(v) <= kDfCoefMax); };
+  // coefficient range of the pools: it fixes the input window of the
+  // double-float arithmetic (df_window)
+  double cmin = HUGE_VAL, cmax = 0.0;
+  auto see = [&](double v) {
+    const double a = std::fabs(v);
+    if (a == 0.0) return;
+    cmin = std::min(cmin, a);
+    cmax = std::max(cmax, a);
+  };
   for (const HostTables* H : {&Hf, &Ht}) {
-    for (double v : H->tab) out.df_ok = out.df_ok && in_window(v);
-    for (double v : H->diag) out.df_ok = out.df_ok && in_window(v);
-    for (double v : H->ell) out.df_ok = out.df_ok && in_window(v);
+    for (double v : H->tab) see(v);
+    for (double v : H->diag) see(v);
+    for (double v : H->ell) see(v);
   }
+  out.cmin = cmax > 0.0 ? cmin : 0.0;
+  out.cmax = cmax;
   return HM_OK;
+}
+
+// Input window of the double-float arithmetic for a coefficient range
+// [cmin, cmax]: every product c x then lies in [2^-100, 2^120), so its
+// rounding error and the split's low parts are normal floats (relative
+// accuracy ~2^-46) and sums of a few hundred products stay finite; x itself
+// must split into normal floats ([2^-100, 2^126)). Empty window (lo >= hi):
+// native FP64 only.
+void df_window(double cmin, double cmax, double* lo, double* hi) {
+  double l = std::ldexp(1.0, -100), h = std::ldexp(1.0, 126);
+  if (cmax > 0.0) {
+    l = std::max(l, std::ldexp(1.0, -100) / cmin);
+    h = std::min(h, std::ldexp(1.0, 120) / cmax);
+  }
+  *lo = l;
+  *hi = h;
 }
 
 // Upload the tables of `hd` (derived for p's split) into one fresh device
@@ -848,7 +914,8 @@ int build_plan(Plan* p) {
   free_plan_device(p);
   free_tiles(p);
   free_streams(p);
-  p->df_ok = hd.df_ok;
+  df_window(hd.cmin, hd.cmax, &p->df_xlo, &p->df_xhi);
+  p->df_ok = p->df_xlo < p->df_xhi;
   rc = upload_tables(p, hd, &p->dev, &p->dev_bytes, &p->k, &p->kt);
   if (rc) {
     p->dev = nullptr;
@@ -894,7 +961,8 @@ const StreamSet* get_stream(Plan* p, long long nvec, cudaStream_t s, bool* defer
     return nullptr;  // not cached: a later call may find memory
   }
   ss.ok = true;
-  ss.df_ok = hd.df_ok;
+  df_window(hd.cmin, hd.cmax, &ss.df_xlo, &ss.df_xhi);
+  ss.df_ok = ss.df_xlo < ss.df_xhi;
   p->streams[nvec] = ss;
   return &p->streams[nvec];
 }
