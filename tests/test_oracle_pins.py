@@ -371,6 +371,26 @@ def test_tavis_cummings_ground_state_is_the_vacuum(nspins):
     assert ws[0] < -nspins / 2 - 0.1
 
 
+def test_counter_based_inputs_match_published_splitmix64_outputs():
+    """x_i is built from output i+1 of splitmix64 seeded with the seed:
+    (z >> 11) * 2^-53 - 1/2. The oracle's generator reproduces the
+    generator's published outputs (a wrong constant, shift or counter offset
+    fails here), and its FP32 form is that value rounded to float."""
+    rows = []
+    with open(os.path.join(GOLDEN, "splitmix64_outputs.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                seed, k, z = (int(t) for t in line.split())
+                rows.append((seed, k, z))
+    assert len(rows) == 8
+    for seed, k, z in rows:
+        want = float(z >> 11) * 2.0 ** -53 - 0.5
+        got = oracle.hashed_values(seed, np.array([k - 1]), False)[0]
+        assert got == want, (seed, k)
+        got32 = oracle.hashed_values(seed, np.array([k - 1]), True)[0]
+        assert got32 == float(np.float32(want)), (seed, k)
+
+
 def test_counter_based_inputs_agree_between_oracle_and_inputs_module():
     """The synthesised vector of the large sampled tests: the oracle's C
     generator and the inputs module's numpy generator (both written from the
