@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "general", "staged"],
                     help="--profile only: force one apply kernel (auto: library or tuned choice)")
+    ap.add_argument("--apply-ex", default=None,
+                    help="--profile only: JSON keyword arguments of Hamiltonian.apply_ex for every timed "
+                         "apply, e.g. '{\"kernel\": \"general\", \"prefetch\": true, \"s\": 8}'")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="use the library's default launch shape instead of autotuning it first")
     return ap.parse_args()
@@ -107,10 +110,14 @@ def run_profile(args):
     total = m.meta.get("sector_total")
     h = Hamiltonian(m.sites, m.terms, sector_total=total)
     dt = torch.float64 if args.dtype == "f64" else torch.float32
-    cfg = h.tune(1, dt) if args.tune and args.kernel == "auto" and total is None else None
+    fixed = json.loads(args.apply_ex) if args.apply_ex else None
+    cfg = h.tune(1, dt) if args.tune and args.kernel == "auto" and total is None and fixed is None else None
     x = W.torch_vector(h.D, 3, dtype=dt)
     y = torch.empty_like(x)
-    if args.kernel == "auto":
+    if fixed is not None:
+        def step():
+            h.apply_ex(x, out=y, **fixed)
+    elif args.kernel == "auto":
         def step():
             h.apply(x, out=y)
     else:
@@ -135,7 +142,7 @@ def run_profile(args):
         nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
-    print(json.dumps({"profile": args.workload, "dtype": args.dtype, "kernel": args.kernel, "D": h.D,
+    print(json.dumps({"profile": args.workload, "dtype": args.dtype, "kernel": fixed or args.kernel, "D": h.D,
                       "ms_per_apply": ms, "gstates_s": h.D / ms / 1e6, "tuned": cfg}))
 
 
@@ -150,9 +157,10 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
+    # the sources the general apply kernel (plain and prefetching) and the
+    # split pass compile from
     for f in ("apply.cu", "apply_kernel.cuh", "apply_launch.cuh", "apply_df64.cu", "apply_f32.cu",
-              "device_common.cuh", "plan.cpp", "hm_internal.h", "stream_kernel.cuh", "stream_launch.cuh",
-              "tma.cuh"):
+              "apply_pf_df64.cu", "apply_pf_f32.cu", "device_common.cuh", "plan.cpp", "hm_internal.h"):
         with open(os.path.join(ROOT, "paper_2606_02169_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -36,7 +36,7 @@
 namespace hm {
 
 #ifndef HM_SRING
-#define HM_SRING 6
+#define HM_SRING 4
 #endif
 constexpr int kSRing = HM_SRING;  // ring slots per CTA
 constexpr int kSDesc = 3;         // block descriptors in flight

@@ -11,17 +11,20 @@
 
 namespace hm {
 
-#ifndef HM_SNC
-#define HM_SNC 4
-#endif
-constexpr int kStreamNC = HM_SNC;  // consumer warps per CTA
+// Consumer warps per CTA: 8 for double-float and native FP64 arithmetic,
+// 4 for FP32 (the faster of 4 and 8 on the chain and spin-boson workloads).
+template <int AR>
+constexpr int stream_nc() {
+  return AR == AR_F32 ? 4 : 8;
+}
 
 template <int AR, int S, bool NV1>
 static cudaError_t stream_nv(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, int ctas,
                              KGate gate) {
   using TX = typename Ar<AR>::TX;
   using TY = typename Ar<AR>::TY;
-  auto kern = k_stream<AR, S, kStreamNC, NV1>;
+  constexpr int NC = stream_nc<AR>();
+  auto kern = k_stream<AR, S, NC, NV1>;
   const size_t smem = stream_layout<AR>(k).total;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static size_t attr_set = 0;
@@ -30,7 +33,7 @@ static cudaError_t stream_nv(const KPlan& k, const void* x, void* y, long long n
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  const int nt = 32 * (kStreamNC + 2);
+  const int nt = 32 * (NC + 2);
   long long grid = ctas;
   if (grid <= 0) {
     int occ = 0;
@@ -46,7 +49,8 @@ template <int AR>
 cudaError_t launch_stream_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg) {
   const long long E = (long long)k.B * nvec;
   if (E > kStreamElems) return cudaErrorInvalidConfiguration;
-  const long long per = (E + 32 * kStreamNC - 1) / (32 * kStreamNC);  // elements per consumer thread
+  constexpr int NC = stream_nc<AR>();
+  const long long per = (E + 32 * NC - 1) / (32 * NC);  // elements per consumer thread
   const bool nv1 = nvec == 1;
   const KGate g{cfg.gate, cfg.gate_run};
   if (per <= 1) return nv1 ? stream_nv<AR, 1, true>(k, x, y, nvec, st, cfg.ctas, g)
