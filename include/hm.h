@@ -148,13 +148,21 @@ int32_t hm_num_terms(hm_handle h);
  * for later calls (hm_destroy hands the unused part back). Inside a stream
  * capture the scratch becomes the graph's own allocation.
  * FP64 arithmetic: by default a double-float sum on the FP32 pipe (error-free
- * products and sums, ~2^-46 relative per product), valid while every nonzero
- * input |x| lies in [2^-70, 2^71) and every coefficient (table entry) in
- * [2^-30, 2^30]. The split pass checks x on the device: if any element is
- * outside (or subnormal, Inf, NaN) the double-float launch stands down and a
- * second launch queued behind it computes the same call in native FP64, so
- * results keep FP64's range for every input; a plan whose coefficients leave
- * the window always computes in native FP64.
+ * products and sums, ~2^-46 relative per product), valid while every
+ * product of a nonzero input and a nonzero coefficient (merged table entry,
+ * magnitudes in [cmin, cmax]) stays in [2^-100, 2^120): the plan's input
+ * window is |x| in [max(2^-100, 2^-100/cmin), min(2^126, 2^120/cmax)), plus
+ * x = 0. The split pass checks x on the device: if any element is outside
+ * (or subnormal, Inf, NaN) the double-float launch stands down and a second
+ * launch queued behind it computes the same call in native FP64, so results
+ * keep FP64's range for every input; a plan whose window is empty always
+ * computes in native FP64. Merged coefficients whose terms cancel to within
+ * 16 ulps of the largest contribution are exactly zero.
+ * nvec a multiple of 4 (FP32) or 2 (FP32, FP64 double-float) with x and y
+ * aligned to 4 or 2 elements: each lane of the general kernel handles that
+ * many consecutive right-hand sides of one state (wider loads, one decode
+ * and one coefficient per state); results are bit-identical to one
+ * right-hand side per lane.
  * Kernel: the general kernel (block-uniform hops as coalesced gathers, hops
  * inside the low block from a per-plan table) unless hm_tune chose another:
  * the general kernel on a small low block, or the staged kernel (each hop's
@@ -181,8 +189,20 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
  * the small low block (B * nvec <= 1024 states, the staged kernel's split)
  * whose per-plan tables stay in L1. Bit 12 (general kernel only): prefetch
  * each thread's gathers four hops ahead with per-thread asynchronous copies
- * into shared memory (elements per thread 4, 6 or 8). ctas > 0 forces the
- * persistent grid size (0 = library default).
+ * into shared memory (elements per thread 4, 6 or 8). Bit 13 (general
+ * kernel only): one right-hand side per lane even where hm_apply would
+ * process 2 or 4 per lane (bit-identical either way). Bit 14 (general
+ * kernel, not with bits 0 or 7): top-site split -- the terms with an
+ * off-diagonal operator on one of the leading T sites run as a second pass
+ * that adds to y and visits the low blocks with those T digits varying
+ * fastest, so that each pass reads x from DRAM about once; T = bits
+ * 16..19, or 0 for every leading site whose hop distance M_k * nvec * element
+ * size is at least 32 MiB (at most 512 digit combinations).
+ * HM_ERR_UNSUPPORTED when the plan has no such split (no term moves a
+ * leading digit, a pass would be empty, or a leading site lies in the low
+ * block). Results differ from the one-pass kernel by rounding only (each
+ * pass rounds once). ctas > 0 forces the persistent grid size (0 = library
+ * default).
  * Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
@@ -313,7 +333,8 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
 /* The launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
  * out[1] = elements per thread (general) or rows per iteration (tile),
  * out[2] = bit 0 register-cap variant, bit 1 small low block, bit 2
- * prefetching (general kernel),
+ * prefetching, bit 3 one right-hand side per lane, bit 4 top-site split,
+ * bits 8..11 its number of leading sites (general kernel),
  * out[3] = kernel (1 general, 2 tile, 3 staged) (int32_t[4], host; 0 each =
  * library default). No counterpart in the paper (a diagnostic). */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);

@@ -1,7 +1,8 @@
 // Host entry points of the apply path: dtype dispatch, the FP64 split pass,
 // device properties and the batched launch. The kernels live in
 // apply_kernel.cuh and are instantiated per arithmetic policy in
-// apply_f32.cu / apply_df64.cu / apply_f64.cu.
+// apply_f32.cu / apply_df64.cu / apply_f64.cu / apply_v_f32.cu /
+// apply_v_df64.cu.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -170,6 +171,27 @@ int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const f
   return HM_OK;
 }
 
+static bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+// The general kernel with the widest policy the call allows: 4 or 2
+// right-hand sides of one state per element when nvec is a multiple and the
+// vectors are aligned to the wider loads (bit-identical to the scalar
+// policy), else one element per thread.
+static cudaError_t launch_general(const KPlan& k, const void* x, void* y, long long nvec, hm_dtype dt, bool native,
+                                  cudaStream_t s, const TuneCfg& c) {
+  if (dt == HM_F32) {
+    if (!c.scalar && nvec % 4 == 0 && aligned(x, 16) && aligned(y, 16))
+      return launch_apply_t<AR_F32V4>(k, x, y, nvec / 4, s, c);
+    if (!c.scalar && nvec % 2 == 0 && aligned(x, 8) && aligned(y, 8))
+      return launch_apply_t<AR_F32V2>(k, x, y, nvec / 2, s, c);
+    return launch_apply_t<AR_F32>(k, x, y, nvec, s, c);
+  }
+  if (native) return launch_apply_t<AR_F64>(k, x, y, nvec, s, c);
+  if (!c.scalar && nvec % 2 == 0 && aligned(x, 16) && aligned(y, 16))
+    return launch_apply_t<AR_DF64V2>(k, x, y, nvec / 2, s, c);
+  return launch_apply_t<AR_DF64>(k, x, y, nvec, s, c);
+}
+
 // y = H x (or H^T x) on stream s. Kernels: cfg.kern = 0 or 1 the general
 // kernel (on the plan's low block, or with cfg.small on the small one), 2 the
 // tile kernel, 3 the staged kernel (autotuner candidates). A strict request
@@ -191,6 +213,18 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
   if (cfg.kern == 3 && !ss && cfg.strict) {
     set_error("this plan has no staged form for that nvec (a site above the slot size, or tables that cannot be "
               "built during stream capture)");
+    return HM_ERR_UNSUPPORTED;
+  }
+  // top-site split (general kernel on the plan's own low block)
+  const SplitSet* sp = nullptr;
+  if (cfg.split && (cfg.kern == 0 || cfg.kern == 1) && !small && !native_f64) {
+    const int T = cfg.split_T ? cfg.split_T : split_top_sites(p, nvec, dt == HM_F32 ? 4 : 8);
+    sp = T > 0 ? get_split(p, T, s) : nullptr;
+    if (sp && dt == HM_F64 && !cfg.presplit && !sp->df_ok) sp = nullptr;
+  }
+  if (cfg.split && !sp && cfg.strict) {
+    set_error("this plan has no top-site split for that request (no term moves a leading site's digit, a "
+              "pass without terms, a leading site inside the low block, native FP64, or a stream capture)");
     return HM_ERR_UNSUPPORTED;
   }
   const KTile* tk = cfg.kern == 2 ? get_tile(p, nvec, transpose, s) : nullptr;
@@ -219,6 +253,10 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
         xlo = std::max(xlo, t->df_xlo);
         xhi = std::min(xhi, t->df_xhi);
       }
+    if (sp) {
+      xlo = std::max(xlo, sp->df_xlo);
+      xhi = std::min(xhi, sp->df_xhi);
+    }
     const float2* xs = nullptr;
     int rc = split_vector(x, vec_states(p) * nvec, s, xsb, &xs, &range, xlo, xhi);
     if (rc) return rc;
@@ -247,19 +285,25 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
       return HM_ERR_UNSUPPORTED;
     }
   }
+  // the general kernel's plan: the whole operator, or pass A of the split
+  const KPlan& kA = sp ? (transpose ? sp->kat : sp->ka) : kg;
   if (e == cudaErrorInvalidConfiguration && gcfg.pf) {
-    if (dt == HM_F32) e = launch_apply_pf_t<AR_F32>(kg, xin, y, nvec, s, gcfg);
-    else if (native_f64) e = launch_apply_pf_t<AR_F64>(kg, xin, y, nvec, s, gcfg);
-    else e = launch_apply_pf_t<AR_DF64>(kg, xin, y, nvec, s, gcfg);
+    if (dt == HM_F32) e = launch_apply_pf_t<AR_F32>(kA, xin, y, nvec, s, gcfg);
+    else if (native_f64) e = launch_apply_pf_t<AR_F64>(kA, xin, y, nvec, s, gcfg);
+    else e = launch_apply_pf_t<AR_DF64>(kA, xin, y, nvec, s, gcfg);
     if (e == cudaErrorInvalidConfiguration && cfg.strict) {
       set_error("prefetching general kernel needs more shared memory than a CTA has");
       return HM_ERR_UNSUPPORTED;
     }
   }
-  if (e == cudaErrorInvalidConfiguration) {
-    if (dt == HM_F32) e = launch_apply_t<AR_F32>(kg, xin, y, nvec, s, gcfg);
-    else if (native_f64) e = launch_apply_t<AR_F64>(kg, xin, y, nvec, s, gcfg);
-    else e = launch_apply_t<AR_DF64>(kg, xin, y, nvec, s, gcfg);
+  if (e == cudaErrorInvalidConfiguration) e = launch_general(kA, xin, y, nvec, dt, native_f64, s, gcfg);
+  if (e == cudaSuccess && sp) {
+    // pass B adds the top-site hops to y; default launch shape, same gate
+    TuneCfg bc{};
+    bc.gate = gcfg.gate;
+    bc.gate_run = gcfg.gate_run;
+    bc.scalar = gcfg.scalar;
+    e = launch_general(transpose ? sp->kbt : sp->kb, xin, y, nvec, dt, native_f64, s, bc);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   if (range) {  // native FP64 fallback, runs only when the split flagged x
@@ -358,6 +402,7 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
       TuneCfg c = tuned_cfg(p, dt, nvec);
       if (c.kern != 1) c = TuneCfg{};
       c.kern = 1;
+      c.split = 0;  // one pass, like the queued members
       int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, c, false);
       if (rc) return rc;
       continue;
@@ -374,8 +419,21 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
     }
   }
   if (mem.empty()) return HM_OK;
-  cudaError_t e = dt == HM_F32 ? launch_batch_t<AR_F32>(mem, sx.data(), sy.data(), nvec, s)
-                               : launch_batch_t<AR_DF64>(mem, sx.data(), sy.data(), nvec, s);
+  // the widest policy every queued member's vectors allow (bit-identical)
+  bool a16 = true, a8 = true;
+  for (size_t i = 0; i < mem.size(); ++i) {
+    a16 = a16 && aligned(sx[i], 16) && aligned(sy[i], 16);
+    a8 = a8 && aligned(sx[i], 8) && aligned(sy[i], 8);
+  }
+  cudaError_t e;
+  if (dt == HM_F32) {
+    if (nvec % 4 == 0 && a16) e = launch_batch_t<AR_F32V4>(mem, sx.data(), sy.data(), nvec / 4, s);
+    else if (nvec % 2 == 0 && a8) e = launch_batch_t<AR_F32V2>(mem, sx.data(), sy.data(), nvec / 2, s);
+    else e = launch_batch_t<AR_F32>(mem, sx.data(), sy.data(), nvec, s);
+  } else {
+    if (nvec % 2 == 0 && a16) e = launch_batch_t<AR_DF64V2>(mem, sx.data(), sy.data(), nvec / 2, s);
+    else e = launch_batch_t<AR_DF64>(mem, sx.data(), sy.data(), nvec, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return HM_OK;
 }

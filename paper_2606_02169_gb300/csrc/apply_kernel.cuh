@@ -30,9 +30,11 @@ constexpr int kNT = 256;  // threads per CTA of the apply kernels
 // tracked per thread (commit / wait_group) with no barrier between threads.
 template <class TX>
 __device__ __forceinline__ void cp_async_elem(TX* dst, const TX* src) {
-  static_assert(sizeof(TX) == 4 || sizeof(TX) == 8, "element size");
+  static_assert(sizeof(TX) == 4 || sizeof(TX) == 8 || sizeof(TX) == 16, "element size");
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(TX) == 8)
+  if constexpr (sizeof(TX) == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else if constexpr (sizeof(TX) == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
@@ -420,11 +422,28 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
       }
     }
   }
-  // ---- store: one write per output element ----
+  // ---- store: one write per output element (the second pass of a
+  //      top-site split adds its rounded sum to the first pass's value) ----
   TY* __restrict__ yb = y + ebase + e0;
+  if (P.accum) {
 #pragma unroll
-  for (int s = 0; s < S; ++s)
-    if (FULL || ok[s]) yb[s * NT] = A::out(acc[s]);
+    for (int s = 0; s < S; ++s)
+      if (FULL || ok[s]) yb[s * NT] = A::add_out(yb[s * NT], A::out(acc[s]));
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (FULL || ok[s]) yb[s * NT] = A::out(acc[s]);
+  }
+}
+
+// Low block visited at position q of a launch: q itself, or, for the second
+// pass of a top-site split, the block whose leading tperm_T digits are
+// q mod R (R their combinations) and whose other high digits are q / R.
+__device__ __forceinline__ long long visit_block(const KPlan& P, long long q) {
+  if (P.tperm_T <= 0) return q;
+  const long long Mt = P.sites[P.tperm_T - 1].mh;  // blocks per top-digit combination
+  const long long R = P.nblk / Mt;
+  return (q % R) * Mt + q / R;
 }
 
 // A block of belems elements is cut into nS chunks of NT*S elements, then n1
@@ -461,6 +480,7 @@ __device__ __forceinline__ void apply_item(const KPlan& P, const Lists<AR>& L, c
 // or one more (MBV = 1, fewer registers per thread); the autotuner picks.
 template <int AR, int MBV> struct MinBlocks { static constexpr int v = 2 + MBV; };
 template <int MBV> struct MinBlocks<AR_F32, MBV> { static constexpr int v = 4 + MBV; };
+template <int MBV> struct MinBlocks<AR_F32V2, MBV> { static constexpr int v = 2 + MBV; };
 
 // bytes of the per-thread prefetch stages of the PF variant, placed after
 // the block lists
@@ -497,29 +517,32 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
     // CTA shares that round
     long long full = (P.nblk / gridDim.x) * gridDim.x;
     if (2 * (P.nblk - full) >= gridDim.x) full = P.nblk;
-    for (long long blk = blockIdx.x; blk < full; blk += gridDim.x) {
+    for (long long q = blockIdx.x; q < full; q += gridDim.x) {
+      const long long blk = visit_block(P, q);
       eval_block<AR>(P, L, blk, nvec);
       for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, c, pfbuf);
       __syncthreads();
     }
     const long long rest = (P.nblk - full) * nchunks;
     for (long long w = blockIdx.x; w < rest; w += gridDim.x) {
-      const long long blk = full + w / nchunks;
+      const long long q = full + w / nchunks;
+      const long long blk = visit_block(P, q);
       if (blk != cur) {
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (blk - full) * nchunks), pfbuf);
+      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (q - full) * nchunks), pfbuf);
       __syncthreads();
     }
   } else {
     for (long long w = blockIdx.x; w < nitems; w += gridDim.x) {
-      const long long blk = w / nchunks;
+      const long long q = w / nchunks;
+      const long long blk = visit_block(P, q);
       if (blk != cur) {
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - blk * nchunks), pfbuf);
+      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - q * nchunks), pfbuf);
       __syncthreads();
     }
   }

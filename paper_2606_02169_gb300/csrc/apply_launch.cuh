@@ -16,10 +16,11 @@ struct Shape {
 // Elements per thread of the main chunks of a block of `belems` elements:
 // the most work in full S-chunks (more loads in flight per thread), the
 // remainder in single-element chunks (see chunk_plan).
-inline Shape pick_shape(long long belems) {
+inline Shape pick_shape(long long belems, int smax = 8) {
   Shape best{2, chunk_plan((int)belems, 2).count()};
   double bs = 0.0;
   for (int s : {8, 6, 4, 3, 2}) {
+    if (s > smax) continue;
     const ChunkPlan cp = chunk_plan((int)belems, s);
     const double frac = (double)cp.nS * kNT * s / (double)belems;   // share in S-chunks
     const double score = frac * (1.0 + 0.02 * s);
@@ -75,11 +76,19 @@ static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long n
   return cudaGetLastError();
 }
 
+// 16-byte elements (4 FP32 or 2 double-float right-hand sides per lane):
+// at most 4 of them per thread and no register-capped variant (both would
+// spill their accumulators).
+template <int AR>
+constexpr bool wide_elem() {
+  return sizeof(typename Ar<AR>::TX) == 16;
+}
+
 template <int AR, int S, int PF>
 static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
                                 cudaStream_t st, TuneCfg cfg) {
   const KGate g{cfg.gate, cfg.gate_run};
-  if constexpr (AR != AR_F64) {
+  if constexpr (AR != AR_F64 && !wide_elem<AR>()) {
     if (cfg.mb) {
       if (nvec == 1) return launch_nv<AR, S, true, 1, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
       return launch_nv<AR, S, false, 1, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
@@ -96,12 +105,23 @@ template <int AR>
 cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg) {
   Shape sh = pick_shape((long long)k.B * nvec);
   if (cfg.s) sh = {cfg.s, chunk_plan((int)(k.B * nvec), cfg.s).count()};
-  switch (sh.s) {
-    case 8: return launch_shape<AR, 8, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-    case 6: return launch_shape<AR, 6, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-    case 4: return launch_shape<AR, 4, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-    case 3: return launch_shape<AR, 3, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-    default: return launch_shape<AR, 2, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+  if constexpr (wide_elem<AR>()) {
+    if (!cfg.s) sh = pick_shape((long long)k.B * nvec, 4);
+    const int s = std::min(sh.s, 4);
+    const int nc = chunk_plan((int)(k.B * nvec), s).count();
+    switch (s) {
+      case 4: return launch_shape<AR, 4, 0>(k, x, y, nvec, nc, st, cfg);
+      case 3: return launch_shape<AR, 3, 0>(k, x, y, nvec, nc, st, cfg);
+      default: return launch_shape<AR, 2, 0>(k, x, y, nvec, nc, st, cfg);
+    }
+  } else {
+    switch (sh.s) {
+      case 8: return launch_shape<AR, 8, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 6: return launch_shape<AR, 6, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 4: return launch_shape<AR, 4, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 3: return launch_shape<AR, 3, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+      default: return launch_shape<AR, 2, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+    }
   }
 }
 
@@ -180,13 +200,21 @@ cudaError_t launch_batch_t(const std::vector<const Plan*>& members, const void* 
   std::vector<long long> be;
   for (const Plan* p : members) be.push_back((long long)p->B * nvec);
   std::nth_element(be.begin(), be.begin() + be.size() / 2, be.end());
-  const Shape sh = pick_shape(be[be.size() / 2]);
-  switch (sh.s) {
-    case 8: return batch_shape<AR, 8>(members, xs, ys, nvec, st);
-    case 6: return batch_shape<AR, 6>(members, xs, ys, nvec, st);
-    case 4: return batch_shape<AR, 4>(members, xs, ys, nvec, st);
-    case 3: return batch_shape<AR, 3>(members, xs, ys, nvec, st);
-    default: return batch_shape<AR, 2>(members, xs, ys, nvec, st);
+  const Shape sh = pick_shape(be[be.size() / 2], wide_elem<AR>() ? 4 : 8);
+  if constexpr (wide_elem<AR>()) {
+    switch (sh.s) {
+      case 4: return batch_shape<AR, 4>(members, xs, ys, nvec, st);
+      case 3: return batch_shape<AR, 3>(members, xs, ys, nvec, st);
+      default: return batch_shape<AR, 2>(members, xs, ys, nvec, st);
+    }
+  } else {
+    switch (sh.s) {
+      case 8: return batch_shape<AR, 8>(members, xs, ys, nvec, st);
+      case 6: return batch_shape<AR, 6>(members, xs, ys, nvec, st);
+      case 4: return batch_shape<AR, 4>(members, xs, ys, nvec, st);
+      case 3: return batch_shape<AR, 3>(members, xs, ys, nvec, st);
+      default: return batch_shape<AR, 2>(members, xs, ys, nvec, st);
+    }
   }
 }
 

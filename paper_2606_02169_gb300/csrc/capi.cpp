@@ -261,8 +261,20 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
   cfg.presplit = (flags >> 6) & 1;
   cfg.small = (flags >> 7) & 1;
   cfg.pf = (flags >> 12) & 1;
-  if ((cfg.small || cfg.pf) && (tile || staged)) {
-    set_error("flag bits 7 and 12 (small low block, prefetching) apply to the general kernel only");
+  cfg.scalar = (flags >> 13) & 1;
+  cfg.split = (flags >> 14) & 1;
+  cfg.split_T = (flags >> 16) & 15;
+  if ((cfg.small || cfg.pf || cfg.scalar || cfg.split) && (tile || staged)) {
+    set_error("flag bits 7, 12, 13 and 14 (small low block, prefetching, one right-hand side per element, "
+              "top-site split) apply to the general kernel only");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (cfg.split_T && !cfg.split) {
+    set_error("flag bits 16..19 (leading sites of a split) need bit 14");
+    return HM_ERR_INVALID_ARG;
+  }
+  if (cfg.split && (cfg.small || (flags & 1))) {
+    set_error("the top-site split runs on the plan's own low block with the double-float or FP32 arithmetic");
     return HM_ERR_INVALID_ARG;
   }
   if (cfg.pf && cfg.s && cfg.s != 4 && cfg.s != 6 && cfg.s != 8) {
@@ -412,6 +424,7 @@ static void destroy_plan(Plan* p) {
   free_plan_device(p);
   free_tiles(p);
   free_streams(p);
+  free_splits(p);
   free_sector(p);
   if (p->scratch) cudaFree(p->scratch);
   p->magic = 0;
@@ -536,6 +549,31 @@ static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
       if (t < tbest) { tbest = t; best = c; }
     }
   }
+  // the best general-kernel shape again as a top-site split, where the
+  // vectors are large enough for one
+  if (rc == HM_OK && best.kern == 1 && !best.small && split_top_sites(p, nvec, esize(dtype)) > 0) {
+    TuneCfg c = best;
+    c.split = 1;
+    c.strict = 1;
+    const float t = time_cfg(c);
+    if (rc == HM_ERR_UNSUPPORTED) rc = HM_OK;
+    else if (t < tbest) { tbest = t; best = c; }
+  }
+  // nvec even: the calls above ran 2 or 4 right-hand sides per lane; one per
+  // lane (bit-identical) is a candidate too
+  if (nvec % 2 == 0) {
+    for (int sh : {4, 6, 8}) {
+      for (int mb = 0; mb < 2 && rc == HM_OK; ++mb) {
+        TuneCfg c;
+        c.kern = 1;
+        c.s = sh;
+        c.mb = mb;
+        c.scalar = 1;
+        const float t = time_cfg(c);
+        if (t < tbest) { tbest = t; best = c; }
+      }
+    }
+  }
   if (rc == HM_OK && get_tile(p, nvec, false, s)) {
     for (int rs : {1, 2, 4}) {
       if (rc != HM_OK) break;
@@ -602,7 +640,7 @@ int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) 
   const TuneCfg c = tuned_cfg(p, dtype, nvec);
   out[0] = c.ctas;
   out[1] = c.s;
-  out[2] = c.mb | (c.small << 1) | (c.pf << 2);
+  out[2] = c.mb | (c.small << 1) | (c.pf << 2) | (c.scalar << 3) | (c.split << 4) | (c.split_T << 8);
   out[3] = c.kern;
   return HM_OK;
 }

@@ -11,6 +11,12 @@
 //             2^-46 per product; the result is rebuilt as a double with one
 //             FP64 add.
 //   AR_F64  : FP64 storage, native FP64 accumulation (reference variant).
+//   AR_F32V2, AR_F32V4, AR_DF64V2: the AR_F32 / AR_DF64 arithmetic on 2 or 4
+//             consecutive right-hand sides of one state per kernel element
+//             (8- or 16-byte loads and stores; decode, table lookups and
+//             coefficients once per state instead of once per right-hand
+//             side). Each right-hand side takes exactly the scalar policy's
+//             operations in the same order, so results are bit-identical.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,7 +26,7 @@
 
 namespace hm {
 
-enum { AR_F32 = 0, AR_DF64 = 1, AR_F64 = 2 };
+enum { AR_F32 = 0, AR_DF64 = 1, AR_F64 = 2, AR_F32V2 = 3, AR_F32V4 = 4, AR_DF64V2 = 5 };
 
 // Launch gate: a kernel runs iff flag == NULL or (*flag != 0) == run. A
 // double-float apply (run = 0) and its native FP64 fallback (run = 1) are
@@ -149,6 +155,7 @@ template <> struct Ar<AR_F32> {
   __device__ static void dmadd(Dsum& d, C v, Dsum u) { d = __fmaf_rn(v, u, d); }
   __device__ static void acc_mul(Acc& a, C v, Acc g) { a = __fmaf_rn(v, g, a); }
   __device__ static TY out(Acc a) { return a; }
+  __device__ static TY add_out(TY a, TY b) { return __fadd_rn(a, b); }
 };
 
 template <> struct Ar<AR_F64> {
@@ -172,6 +179,7 @@ template <> struct Ar<AR_F64> {
   __device__ static void dmadd(Dsum& d, C v, Dsum u) { d = __fma_rn(v, u, d); }
   __device__ static void acc_mul(Acc& a, C v, Acc g) { a = __fma_rn(v, g, a); }
   __device__ static TY out(Acc a) { return a; }
+  __device__ static TY add_out(TY a, TY b) { return __dadd_rn(a, b); }
 };
 
 template <> struct Ar<AR_DF64> {
@@ -205,6 +213,83 @@ template <> struct Ar<AR_DF64> {
     df_fma(a, v, n.x, n.y);
   }
   __device__ static TY out(Acc a) { return df_to_double(a); }
+  __device__ static TY add_out(TY a, TY b) { return __dadd_rn(a, b); }
+};
+
+// Vector policies: TX/TY/Acc hold W right-hand sides of one state; the
+// coefficient, diagonal-sum and ELL types stay the scalar policy's.
+template <> struct Ar<AR_F32V2> : Ar<AR_F32> {
+  using TX = float2;
+  using TY = float2;
+  using Acc = float2;
+  __device__ static Acc azero() { return make_float2(0.f, 0.f); }
+  __device__ static void fma(Acc& a, C c, TX x) {
+    a.x = __fmaf_rn(c, x.x, a.x);
+    a.y = __fmaf_rn(c, x.y, a.y);
+  }
+  __device__ static Acc dmul(Dsum d, TX x) { return make_float2(__fmul_rn(d, x.x), __fmul_rn(d, x.y)); }
+  __device__ static void acc_mul(Acc& a, C v, Acc g) {
+    a.x = __fmaf_rn(v, g.x, a.x);
+    a.y = __fmaf_rn(v, g.y, a.y);
+  }
+  __device__ static TY out(Acc a) { return a; }
+  __device__ static TY add_out(TY a, TY b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+};
+
+template <> struct Ar<AR_F32V4> : Ar<AR_F32> {
+  using TX = float4;
+  using TY = float4;
+  using Acc = float4;
+  __device__ static Acc azero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static void fma(Acc& a, C c, TX x) {
+    a.x = __fmaf_rn(c, x.x, a.x);
+    a.y = __fmaf_rn(c, x.y, a.y);
+    a.z = __fmaf_rn(c, x.z, a.z);
+    a.w = __fmaf_rn(c, x.w, a.w);
+  }
+  __device__ static Acc dmul(Dsum d, TX x) {
+    return make_float4(__fmul_rn(d, x.x), __fmul_rn(d, x.y), __fmul_rn(d, x.z), __fmul_rn(d, x.w));
+  }
+  __device__ static void acc_mul(Acc& a, C v, Acc g) {
+    a.x = __fmaf_rn(v, g.x, a.x);
+    a.y = __fmaf_rn(v, g.y, a.y);
+    a.z = __fmaf_rn(v, g.z, a.z);
+    a.w = __fmaf_rn(v, g.w, a.w);
+  }
+  __device__ static TY out(Acc a) { return a; }
+  __device__ static TY add_out(TY a, TY b) {
+    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+  }
+};
+
+struct DF2 {  // two right-hand sides' double-float accumulators
+  DF a, b;
+};
+
+template <> struct Ar<AR_DF64V2> : Ar<AR_DF64> {
+  using TX = float4;  // (hi, lo) of two consecutive right-hand sides
+  using TY = double2;
+  using Acc = DF2;
+  __device__ static Acc azero() { return DF2{DF{0.f, 0.f}, DF{0.f, 0.f}}; }
+  __device__ static void fma(Acc& a, C c, TX x) {
+    df_fma(a.a, c, x.x, x.y);
+    df_fma(a.b, c, x.z, x.w);
+  }
+  __device__ static Acc dmul(Dsum d, TX x) {
+    const float2 n = df_norm(d);
+    DF2 r = azero();
+    df_fma(r.a, n, x.x, x.y);
+    df_fma(r.b, n, x.z, x.w);
+    return r;
+  }
+  __device__ static void acc_mul(Acc& a, C v, Acc g) {
+    const float2 na = df_norm(g.a);
+    df_fma(a.a, v, na.x, na.y);
+    const float2 nb = df_norm(g.b);
+    df_fma(a.b, v, nb.x, nb.y);
+  }
+  __device__ static TY out(Acc a) { return make_double2(df_to_double(a.a), df_to_double(a.b)); }
+  __device__ static TY add_out(TY a, TY b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
 };
 
 // digit of a high (tile-uniform) site, held by lane (site % 32) in nh0/nh1

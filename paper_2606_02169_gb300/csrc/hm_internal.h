@@ -97,6 +97,12 @@ struct KPlan {
   int ell_w;                   // width of the low-block ELL table
   int nterm_ch;                // per-term channels (adjoint)
   int nterms;
+  // second pass of a top-site split (general kernel only): tperm_T > 0
+  // visits the low blocks with the digits of the leading tperm_T sites
+  // varying fastest, so that the blocks a top-site hop connects are in
+  // flight together; accum = 1 adds the result to y instead of storing it
+  int tperm_T;
+  int accum;
   const KSite* sites;     // [nsites]
   const KChan* ch;
   const KGroup* grp;
@@ -181,6 +187,19 @@ struct KTile {
 
 // Kernel tables of the staged apply kernel for one nvec (H and H^T), in a
 // device allocation of their own.
+// Top-site split of one plan (general kernel): pass A holds every term
+// without an off-diagonal operator on the leading T sites (it writes y),
+// pass B the others (it adds to y, visiting blocks top-digits-fastest).
+// Built on first use per T.
+struct SplitSet {
+  bool ok = false;
+  bool df_ok = true;                   // both passes' double-float windows are non-empty
+  double df_xlo = 0.0, df_xhi = 0.0;   // their intersection
+  KPlan ka{}, kat{}, kb{}, kbt{};      // pass A / pass B, H and H^T
+  void* dev_a = nullptr;
+  void* dev_b = nullptr;
+};
+
 struct StreamSet {
   bool ok = false;
   bool df_ok = true;   // the double-float input window is not empty
@@ -207,6 +226,13 @@ struct TuneCfg {
   // tables (ELL, diagonal, packed digits) stay in L1
   int small = 0;
   int pf = 0;  // general kernel: 1 = prefetch its gathers with cp.async (4 stages)
+  // general kernel: 1 = one right-hand side per element even when nvec and
+  // the vectors' alignment allow the 2- or 4-wide policies
+  int scalar = 0;
+  // general kernel: 1 = top-site split into two passes (SplitSet), with
+  // split_T leading sites (0 = chosen from the vector size, split_top_sites)
+  int split = 0;
+  int split_T = 0;
 };
 
 struct Channel {            // host-side merged channel
@@ -278,6 +304,8 @@ struct Plan {
 
   // staged-kernel (and small-block) tables per nvec, built on first use
   std::map<long long, StreamSet> streams;
+  // top-site splits per number of top sites T, built on first use
+  std::map<int, SplitSet> splits;
 
   // autotuned launch choice per (dtype, nvec); absent = default
   std::map<std::pair<int, long long>, TuneCfg> tuned;
@@ -295,6 +323,13 @@ void free_plan_device(Plan* p);
 // e.g. during stream capture; then *deferred = true)
 const StreamSet* get_stream(Plan* p, long long nvec, cudaStream_t s, bool* deferred = nullptr);
 void free_streams(Plan* p);
+// top-site split with T leading sites (NULL: no split form for T, or not
+// buildable now, e.g. during stream capture)
+const SplitSet* get_split(Plan* p, int T, cudaStream_t s);
+void free_splits(Plan* p);
+// number of leading sites whose hops a split moves to its second pass for
+// vectors of es-byte elements and nvec right-hand sides (0: no split)
+int split_top_sites(const Plan* p, long long nvec, size_t es);
 
 // sector.cu
 int build_sector(Plan* p);   // sector tables from p->chH (after build_plan's host half)

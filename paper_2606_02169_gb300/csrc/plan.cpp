@@ -914,6 +914,7 @@ int build_plan(Plan* p) {
   free_plan_device(p);
   free_tiles(p);
   free_streams(p);
+  free_splits(p);
   df_window(hd.cmin, hd.cmax, &p->df_xlo, &p->df_xhi);
   p->df_ok = p->df_xlo < p->df_xhi;
   rc = upload_tables(p, hd, &p->dev, &p->dev_bytes, &p->k, &p->kt);
@@ -971,6 +972,101 @@ void free_streams(Plan* p) {
   for (auto& kv : p->streams)
     if (kv.second.dev) cudaFree(kv.second.dev);
   p->streams.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Top-site split. A hop along site k reads x at distance M_k; when M_k times
+// the bytes per state exceeds what L2 keeps of x behind the blocks in flight,
+// every such source is read from DRAM a second time. The split applies the
+// terms with an off-diagonal operator (a nonzero digit move, Sec. IV.A) on
+// one of the leading T sites in a second pass that visits the low blocks with
+// those T digits varying fastest: the blocks a top-site hop connects are then
+// in flight together and x is read from DRAM about once per pass.
+// ---------------------------------------------------------------------------
+
+constexpr long long kSplitBytes = 32LL << 20;  // hop distance beyond which L2 misses
+constexpr long long kSplitCombos = 512;        // top-digit combinations visited together
+
+static bool moves_digit(int op) {
+  return op == HM_SX || op == HM_SY || op == HM_SP || op == HM_SM || op == HM_SP2 || op == HM_SM2 ||
+         op == HM_A || op == HM_ADAG;
+}
+
+int split_top_sites(const Plan* p, long long nvec, size_t es) {
+  if (p->sector || p->N < 2) return 0;
+  int T = 0;
+  long long R = 1;
+  while (T < p->N - 1 && (long long)p->M[T] * nvec * (long long)es >= kSplitBytes &&
+         R * p->sites[T].dim <= kSplitCombos) {
+    R *= p->sites[T].dim;
+    ++T;
+  }
+  return T;
+}
+
+const SplitSet* get_split(Plan* p, int T, cudaStream_t s) {
+  auto it = p->splits.find(T);
+  if (it != p->splits.end()) return it->second.ok ? &it->second : nullptr;
+  if (p->sector || T < 1 || T >= p->N) return nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;  // uploading needs synchronous allocation
+  }
+  SplitSet sp;
+  Plan ta, tb;
+  for (Plan* t : {&ta, &tb}) {
+    t->N = p->N;
+    t->sites = p->sites;
+    t->part = p->part;
+    t->device = p->device;
+  }
+  for (const hm_term& tm : p->terms) {
+    const bool top = (tm.site_i < T && moves_digit(tm.op_i)) || (tm.site_j >= 0 && tm.site_j < T && moves_digit(tm.op_j));
+    (top ? tb : ta).terms.push_back(tm);
+  }
+  if (ta.terms.empty() || tb.terms.empty()) {
+    p->splits[T] = sp;  // nothing to split
+    return nullptr;
+  }
+  HostPlanData ha, hb;
+  if (derive_plan(&ta, ha, kLowBlockMax) != HM_OK || derive_plan(&tb, hb, kLowBlockMax) != HM_OK ||
+      (long long)(tb.N - tb.nlow) < T) {
+    cudaGetLastError();
+    p->splits[T] = sp;  // the top sites must be high sites of the second pass
+    return nullptr;
+  }
+  size_t bytes = 0;
+  if (upload_tables(&ta, ha, &sp.dev_a, &bytes, &sp.ka, &sp.kat) != HM_OK) {
+    cudaGetLastError();
+    return nullptr;  // not cached: a later call may find memory
+  }
+  if (upload_tables(&tb, hb, &sp.dev_b, &bytes, &sp.kb, &sp.kbt) != HM_OK) {
+    cudaGetLastError();
+    cudaFree(sp.dev_a);
+    return nullptr;
+  }
+  for (KPlan* k : {&sp.kb, &sp.kbt}) {
+    k->tperm_T = T;
+    k->accum = 1;
+  }
+  double la, ua, lb, ub;
+  df_window(ha.cmin, ha.cmax, &la, &ua);
+  df_window(hb.cmin, hb.cmax, &lb, &ub);
+  sp.df_xlo = std::max(la, lb);
+  sp.df_xhi = std::min(ua, ub);
+  sp.df_ok = sp.df_xlo < sp.df_xhi;
+  sp.ok = true;
+  p->splits[T] = sp;
+  return &p->splits[T];
+}
+
+void free_splits(Plan* p) {
+  for (auto& kv : p->splits) {
+    if (kv.second.dev_a) cudaFree(kv.second.dev_a);
+    if (kv.second.dev_b) cudaFree(kv.second.dev_b);
+  }
+  p->splits.clear();
 }
 
 }  // namespace hm
