@@ -24,6 +24,13 @@ namespace hm {
 
 constexpr int kNT = 256;  // threads per CTA of the apply kernels
 
+// y is written once and not read again by the kernel: streaming stores
+// (evict-first), so that L2 keeps x for the hops of neighbouring blocks.
+template <class T>
+__device__ __forceinline__ void st_y(T* p, T v) {
+  __stcs(p, v);
+}
+
 // Per-thread asynchronous copies (cp.async) of one element from global to
 // shared memory, for the prefetching variant of the general kernel: each
 // thread copies, and later reads, only its own slots, so completion is
@@ -428,11 +435,11 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
   if (P.accum) {
 #pragma unroll
     for (int s = 0; s < S; ++s)
-      if (FULL || ok[s]) yb[s * NT] = A::add_out(yb[s * NT], A::out(acc[s]));
+      if (FULL || ok[s]) st_y(yb + s * NT, A::add_out(yb[s * NT], A::out(acc[s])));
   } else {
 #pragma unroll
     for (int s = 0; s < S; ++s)
-      if (FULL || ok[s]) yb[s * NT] = A::out(acc[s]);
+      if (FULL || ok[s]) st_y(yb + s * NT, A::out(acc[s]));
   }
 }
 
