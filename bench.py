@@ -436,7 +436,7 @@ def kernel_only_ms(h, x, y, cfg, steps, stream):
     if kernel == "general":
         kw.update(small=bool(cfg.get("small", 0)), prefetch=bool(cfg.get("prefetch", 0)),
                   scalar=bool(cfg.get("scalar", 0)), split=bool(cfg.get("split", 0)),
-                  split_sites=cfg.get("split_sites", 0))
+                  split_sites=cfg.get("split_sites", 0), vinv=bool(cfg.get("vinv", 0)))
     xs = split_pairs(x)
     ms = timed(lambda: h.apply_ex(xs, out=y, presplit=True, **kw), steps, 3, 1, stream) / steps
     del xs

@@ -201,8 +201,13 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
  * HM_ERR_UNSUPPORTED when the plan has no such split (no term moves a
  * leading digit, a pass would be empty, or a leading site lies in the low
  * block). Results differ from the one-pass kernel by rounding only (each
- * pass rounds once). ctas > 0 forces the persistent grid size (0 = library
- * default).
+ * pass rounds once). Bit 15 (general kernel): where every factorised
+ * high/low group's low digit is the same for all elements a lane handles
+ * (its period M_k d_k divides their stride), one group factor v per lane
+ * and member coefficients v*u formed once per lane instead of
+ * v * sum(u x) per element (fewer registers and operations; rounds
+ * differently, within the same tolerance); ignored elsewhere. ctas > 0
+ * forces the persistent grid size (0 = library default).
  * Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
@@ -334,7 +339,8 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
  * out[1] = elements per thread (general) or rows per iteration (tile),
  * out[2] = bit 0 register-cap variant, bit 1 small low block, bit 2
  * prefetching, bit 3 one right-hand side per lane, bit 4 top-site split,
- * bits 8..11 its number of leading sites (general kernel),
+ * bit 5 one group factor per lane, bits 8..11 the split's number of
+ * leading sites (general kernel),
  * out[3] = kernel (1 general, 2 tile, 3 staged) (int32_t[4], host; 0 each =
  * library default). No counterpart in the paper (a diagnostic). */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);

@@ -1,8 +1,7 @@
 // Host entry points of the apply path: dtype dispatch, the FP64 split pass,
 // device properties and the batched launch. The kernels live in
-// apply_kernel.cuh and are instantiated per arithmetic policy in
-// apply_f32.cu / apply_df64.cu / apply_f64.cu / apply_v_f32.cu /
-// apply_v_df64.cu.
+// apply_kernel.cuh and are instantiated per arithmetic policy and variant in
+// the apply_*.cu units (apply_launch.cuh).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -13,7 +12,7 @@
 
 namespace hm {
 
-template <int AR>
+template <int AR, bool VI>
 cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
 template <int AR>
 cudaError_t launch_batch_t(const std::vector<const Plan*>& members, const void* const* xs, void* const* ys,
@@ -22,8 +21,21 @@ template <int AR>
 cudaError_t launch_tile_t(const KTile& k, const void* x, void* y, cudaStream_t st, TuneCfg cfg);
 template <int AR>
 cudaError_t launch_stream_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
-template <int AR>
+template <int AR, bool VI>
 cudaError_t launch_apply_pf_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
+
+// The general kernel (PF: prefetching) with the per-thread group factor
+// where the launch asks for it and the plan's groups allow it (FP32 and
+// double-float scalar policies).
+template <int AR, bool PF>
+static cudaError_t general_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t s,
+                             const TuneCfg& c) {
+  if constexpr (AR == AR_F32 || AR == AR_DF64) {
+    if (c.vinv && groups_invariant(k, nvec))
+      return PF ? launch_apply_pf_t<AR, true>(k, x, y, nvec, s, c) : launch_apply_t<AR, true>(k, x, y, nvec, s, c);
+  }
+  return PF ? launch_apply_pf_t<AR, false>(k, x, y, nvec, s, c) : launch_apply_t<AR, false>(k, x, y, nvec, s, c);
+}
 
 static int g_nsm = 0;
 int num_sms() {
@@ -181,15 +193,15 @@ static cudaError_t launch_general(const KPlan& k, const void* x, void* y, long l
                                   cudaStream_t s, const TuneCfg& c) {
   if (dt == HM_F32) {
     if (!c.scalar && nvec % 4 == 0 && aligned(x, 16) && aligned(y, 16))
-      return launch_apply_t<AR_F32V4>(k, x, y, nvec / 4, s, c);
+      return launch_apply_t<AR_F32V4, false>(k, x, y, nvec / 4, s, c);
     if (!c.scalar && nvec % 2 == 0 && aligned(x, 8) && aligned(y, 8))
-      return launch_apply_t<AR_F32V2>(k, x, y, nvec / 2, s, c);
-    return launch_apply_t<AR_F32>(k, x, y, nvec, s, c);
+      return launch_apply_t<AR_F32V2, false>(k, x, y, nvec / 2, s, c);
+    return general_t<AR_F32, false>(k, x, y, nvec, s, c);
   }
-  if (native) return launch_apply_t<AR_F64>(k, x, y, nvec, s, c);
+  if (native) return launch_apply_t<AR_F64, false>(k, x, y, nvec, s, c);
   if (!c.scalar && nvec % 2 == 0 && aligned(x, 16) && aligned(y, 16))
-    return launch_apply_t<AR_DF64V2>(k, x, y, nvec / 2, s, c);
-  return launch_apply_t<AR_DF64>(k, x, y, nvec, s, c);
+    return launch_apply_t<AR_DF64V2, false>(k, x, y, nvec / 2, s, c);
+  return general_t<AR_DF64, false>(k, x, y, nvec, s, c);
 }
 
 // y = H x (or H^T x) on stream s. Kernels: cfg.kern = 0 or 1 the general
@@ -288,9 +300,9 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
   // the general kernel's plan: the whole operator, or pass A of the split
   const KPlan& kA = sp ? (transpose ? sp->kat : sp->ka) : kg;
   if (e == cudaErrorInvalidConfiguration && gcfg.pf) {
-    if (dt == HM_F32) e = launch_apply_pf_t<AR_F32>(kA, xin, y, nvec, s, gcfg);
-    else if (native_f64) e = launch_apply_pf_t<AR_F64>(kA, xin, y, nvec, s, gcfg);
-    else e = launch_apply_pf_t<AR_DF64>(kA, xin, y, nvec, s, gcfg);
+    if (dt == HM_F32) e = general_t<AR_F32, true>(kA, xin, y, nvec, s, gcfg);
+    else if (native_f64) e = launch_apply_pf_t<AR_F64, false>(kA, xin, y, nvec, s, gcfg);
+    else e = general_t<AR_DF64, true>(kA, xin, y, nvec, s, gcfg);
     if (e == cudaErrorInvalidConfiguration && cfg.strict) {
       set_error("prefetching general kernel needs more shared memory than a CTA has");
       return HM_ERR_UNSUPPORTED;
@@ -312,7 +324,7 @@ int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm
     fb.gate_run = 1;
     e = cudaErrorInvalidConfiguration;
     if (ss) e = launch_stream_t<AR_F64>(transpose ? ss->kt : ss->k, x, y, nvec, s, fb);
-    if (e == cudaErrorInvalidConfiguration) e = launch_apply_t<AR_F64>(k, x, y, nvec, s, fb);
+    if (e == cudaErrorInvalidConfiguration) e = launch_apply_t<AR_F64, false>(k, x, y, nvec, s, fb);
     if (e != cudaSuccess) return cuda_fail(e, "apply launch (FP64 fallback)");
   }
   return HM_OK;
@@ -402,7 +414,8 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
       TuneCfg c = tuned_cfg(p, dt, nvec);
       if (c.kern != 1) c = TuneCfg{};
       c.kern = 1;
-      c.split = 0;  // one pass, like the queued members
+      c.split = 0;  // one pass and the queued members' group arithmetic
+      c.vinv = 0;
       int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, c, false);
       if (rc) return rc;
       continue;

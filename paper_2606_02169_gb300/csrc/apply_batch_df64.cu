@@ -1,0 +1,7 @@
+// Instantiations of the batched apply kernel for AR_DF64.
+#include "apply_launch.cuh"
+
+namespace hm {
+template cudaError_t launch_batch_t<AR_DF64>(const std::vector<const Plan*>&, const void* const*, void* const*,
+                                           long long, cudaStream_t);
+}  // namespace hm

@@ -54,10 +54,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // the gathers issued PF items ahead through PF per-thread shared-memory
 // stages (slot (stage, s) of this thread at pf[(stage * S + s) * kNT]).
 // mask[s] = false skips element s (its copy and its FMA).
-template <int AR, int S, int PF>
+// SCALE: the coefficients are vs * c[j] (formed per item, A::cmul).
+template <int AR, int S, int PF, bool SCALE = false>
 __device__ __forceinline__ void pf_sum(typename Ar<AR>::Acc (&acc)[S], const typename Ar<AR>::C* c,
                                        const long long* off, int n, const typename Ar<AR>::TX* base,
-                                       const bool (&mask)[S], typename Ar<AR>::TX* pf) {
+                                       const bool (&mask)[S], typename Ar<AR>::TX* pf,
+                                       typename Ar<AR>::C vs = typename Ar<AR>::C{}) {
   using A = Ar<AR>;
   using TX = typename A::TX;
   static_assert((PF & (PF - 1)) == 0, "PF a power of two");
@@ -74,7 +76,7 @@ __device__ __forceinline__ void pf_sum(typename Ar<AR>::Acc (&acc)[S], const typ
   for (int j = 0; j < n; ++j) {
     cp_async_wait<PF - 1>();
     const int st = j & (PF - 1);
-    const typename A::C cj = c[j];
+    const typename A::C cj = SCALE ? A::cmul(vs, c[j]) : c[j];
 #pragma unroll
     for (int s = 0; s < S; ++s)
       if (mask[s]) A::fma(acc[s], cj, pf[(st * S + s) * kNT]);
@@ -297,7 +299,10 @@ struct NvDiv {
 // One chunk of NT*S elements starting at element `e_start` of low block blk
 // (uniforms already in L). FULL: every element of the chunk lies inside the
 // block, so no per-element bounds predicates are needed. NV1: nvec == 1.
-template <int AR, int S, bool FULL, bool NV1, int PF = 0>
+// VINV: the low digit of every factorised group is the same for the
+// thread's S elements (its period M_k d_k divides their stride), so each
+// group has one v per thread and member coefficients v u are formed once.
+template <int AR, int S, bool FULL, bool NV1, int PF = 0, bool VINV = false>
 __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
                                             const typename Ar<AR>::TX* __restrict__ x,
                                             typename Ar<AR>::TY* __restrict__ y, int nvec_rt, NvDiv nvdiv,
@@ -375,6 +380,26 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
   for (int g = P.n_grp_diag; g < P.n_grp_diag + P.n_grp; ++g) {
     const KGroup gr = L.dgrp[g];
     const int vb = L.grp_v[g];
+    if constexpr (VINV) {
+      const C v0 = tab[vb + low_digit(pk[0], gr.lbit, gr.lwid)];
+      if (!A::nz(v0)) continue;  // inadmissible low digit for all S elements
+      const int na = L.gact_n[g];
+      const C* __restrict__ gu = L.gact_u + gr.m0;
+      const long long* __restrict__ gs = L.gact_src + gr.m0;
+      if constexpr (PF > 0) {
+        pf_sum<AR, S, PF, true>(acc, gu, gs, na, xb, ok, pf, v0);
+      } else {
+#pragma unroll(S >= 6 ? 2 : 4)
+        for (int j = 0; j < na; ++j) {
+          const C c = A::cmul(v0, gu[j]);
+          const TX* __restrict__ src = xb + gs[j];
+#pragma unroll
+          for (int s = 0; s < S; ++s)
+            if (FULL || ok[s]) A::fma(acc[s], c, __ldg(src + s * NT));
+        }
+      }
+      continue;
+    }
     C v[S];
     Acc ag[S];
 #pragma unroll
@@ -470,17 +495,25 @@ __host__ __device__ inline ChunkPlan chunk_plan(int belems, int S) {
   return c;
 }
 
-template <int AR, int S, bool NV1, int PF = 0>
+template <int AR, int S, bool NV1, int PF = 0, bool VINV = false>
 __device__ __forceinline__ void apply_item(const KPlan& P, const Lists<AR>& L, const typename Ar<AR>::TX* x,
                                            typename Ar<AR>::TY* y, int nvec, NvDiv nvdiv, long long blk,
                                            const ChunkPlan& cp, int c, typename Ar<AR>::TX* pfbuf = nullptr) {
   if (c < cp.nS) {
-    apply_chunk<AR, S, true, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, c * kNT * S, pfbuf);
+    apply_chunk<AR, S, true, NV1, PF, VINV>(P, L, x, y, nvec, nvdiv, blk, c * kNT * S, pfbuf);
   } else if (c < cp.nS + cp.n1) {
-    apply_chunk<AR, 1, true, NV1>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + (c - cp.nS) * kNT);
+    apply_chunk<AR, 1, true, NV1, 0, VINV>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + (c - cp.nS) * kNT);
   } else {
-    apply_chunk<AR, 1, false, NV1>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + cp.n1 * kNT);
+    apply_chunk<AR, 1, false, NV1, 0, VINV>(P, L, x, y, nvec, nvdiv, blk, cp.nS * kNT * S + cp.n1 * kNT);
   }
+}
+
+// Every factorised group's low digit is the same for a thread's elements
+// t, t + NT, ...: the digit's period (KPlan::vperiod, in states) divides the
+// stride NT / nvec states (the elements interleave nvec right-hand sides).
+inline bool groups_invariant(const KPlan& k, long long nvec) {
+  if (k.vperiod <= 0 || kNT % nvec != 0) return false;
+  return (kNT / nvec) % k.vperiod == 0;
 }
 
 // Resident CTAs per SM the register allocation must allow: default (MBV = 0)
@@ -498,7 +531,7 @@ __host__ __device__ constexpr size_t pf_bytes() {
 
 // PF = 0: gathers as plain loads; PF > 0: each thread prefetches its gathers
 // of the full-size chunks PF items ahead with cp.async (pf_sum)
-template <int AR, int S, bool NV1, int MBV, int PF = 0>
+template <int AR, int S, bool NV1, int MBV, int PF = 0, bool VINV = false>
 __global__ void __launch_bounds__(kNT, MinBlocks<AR, MBV>::v)
 k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR>::TY* __restrict__ y,
         int nvec, NvDiv nvdiv, KGate gate) {
@@ -527,7 +560,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
     for (long long q = blockIdx.x; q < full; q += gridDim.x) {
       const long long blk = visit_block(P, q);
       eval_block<AR>(P, L, blk, nvec);
-      for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, c, pfbuf);
+      for (int c = 0; c < nchunks; ++c) apply_item<AR, S, NV1, PF, VINV>(P, L, x, y, nvec, nvdiv, blk, cp, c, pfbuf);
       __syncthreads();
     }
     const long long rest = (P.nblk - full) * nchunks;
@@ -538,7 +571,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (q - full) * nchunks), pfbuf);
+      apply_item<AR, S, NV1, PF, VINV>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - (q - full) * nchunks), pfbuf);
       __syncthreads();
     }
   } else {
@@ -549,7 +582,7 @@ k_apply(const KPlan P, const typename Ar<AR>::TX* __restrict__ x, typename Ar<AR
         cur = blk;
         eval_block<AR>(P, L, blk, nvec);
       }
-      apply_item<AR, S, NV1, PF>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - q * nchunks), pfbuf);
+      apply_item<AR, S, NV1, PF, VINV>(P, L, x, y, nvec, nvdiv, blk, cp, (int)(w - q * nchunks), pfbuf);
       __syncthreads();
     }
   }

@@ -49,12 +49,12 @@ inline NvDiv make_nvdiv(long long nvec) {
 
 int num_sms();
 
-template <int AR, int S, bool NV1, int MBV, int PF>
+template <int AR, int S, bool NV1, int MBV, int PF, bool VI>
 static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long nvec, int nchunks, cudaStream_t st,
                              int ctas, KGate gate) {
   using TX = typename Ar<AR>::TX;
   using TY = typename Ar<AR>::TY;
-  auto kern = k_apply<AR, S, NV1, MBV, PF>;
+  auto kern = k_apply<AR, S, NV1, MBV, PF, VI>;
   size_t smem = lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag);
   if (PF > 0) smem = ((smem + 15) & ~size_t(15)) + pf_bytes<AR, S, PF>();
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -84,24 +84,25 @@ constexpr bool wide_elem() {
   return sizeof(typename Ar<AR>::TX) == 16;
 }
 
-template <int AR, int S, int PF>
+template <int AR, int S, int PF, bool VI>
 static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
                                 cudaStream_t st, TuneCfg cfg) {
   const KGate g{cfg.gate, cfg.gate_run};
   if constexpr (AR != AR_F64 && !wide_elem<AR>()) {
     if (cfg.mb) {
-      if (nvec == 1) return launch_nv<AR, S, true, 1, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
-      return launch_nv<AR, S, false, 1, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+      if (nvec == 1) return launch_nv<AR, S, true, 1, PF, VI>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+      return launch_nv<AR, S, false, 1, PF, VI>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
     }
   }
-  if (nvec == 1) return launch_nv<AR, S, true, 0, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
-  return launch_nv<AR, S, false, 0, PF>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+  if (nvec == 1) return launch_nv<AR, S, true, 0, PF, VI>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
+  return launch_nv<AR, S, false, 0, PF, VI>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
 }
+
 
 // Elements-per-thread values the kernels are instantiated for.
 constexpr int kShapes[] = {2, 3, 4, 6, 8};
 
-template <int AR>
+template <int AR, bool VI>
 cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg) {
   Shape sh = pick_shape((long long)k.B * nvec);
   if (cfg.s) sh = {cfg.s, chunk_plan((int)(k.B * nvec), cfg.s).count()};
@@ -110,33 +111,33 @@ cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nve
     const int s = std::min(sh.s, 4);
     const int nc = chunk_plan((int)(k.B * nvec), s).count();
     switch (s) {
-      case 4: return launch_shape<AR, 4, 0>(k, x, y, nvec, nc, st, cfg);
-      case 3: return launch_shape<AR, 3, 0>(k, x, y, nvec, nc, st, cfg);
-      default: return launch_shape<AR, 2, 0>(k, x, y, nvec, nc, st, cfg);
+      case 4: return launch_shape<AR, 4, 0, VI>(k, x, y, nvec, nc, st, cfg);
+      case 3: return launch_shape<AR, 3, 0, VI>(k, x, y, nvec, nc, st, cfg);
+      default: return launch_shape<AR, 2, 0, VI>(k, x, y, nvec, nc, st, cfg);
     }
   } else {
     switch (sh.s) {
-      case 8: return launch_shape<AR, 8, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-      case 6: return launch_shape<AR, 6, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-      case 4: return launch_shape<AR, 4, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-      case 3: return launch_shape<AR, 3, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
-      default: return launch_shape<AR, 2, 0>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 8: return launch_shape<AR, 8, 0, VI>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 6: return launch_shape<AR, 6, 0, VI>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 4: return launch_shape<AR, 4, 0, VI>(k, x, y, nvec, sh.nchunks, st, cfg);
+      case 3: return launch_shape<AR, 3, 0, VI>(k, x, y, nvec, sh.nchunks, st, cfg);
+      default: return launch_shape<AR, 2, 0, VI>(k, x, y, nvec, sh.nchunks, st, cfg);
     }
   }
 }
 
 // The prefetching variant (PF = 4 stages), for 4, 6 or 8 elements per
 // thread (default: the shape pick_shape chooses, rounded to those).
-template <int AR>
+template <int AR, bool VI>
 cudaError_t launch_apply_pf_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg) {
   Shape sh = pick_shape((long long)k.B * nvec);
   int s = cfg.s ? cfg.s : sh.s;
   s = s >= 8 ? 8 : (s >= 6 ? 6 : 4);
   const int nchunks = chunk_plan((int)(k.B * nvec), s).count();
   switch (s) {
-    case 8: return launch_shape<AR, 8, 4>(k, x, y, nvec, nchunks, st, cfg);
-    case 6: return launch_shape<AR, 6, 4>(k, x, y, nvec, nchunks, st, cfg);
-    default: return launch_shape<AR, 4, 4>(k, x, y, nvec, nchunks, st, cfg);
+    case 8: return launch_shape<AR, 8, 4, VI>(k, x, y, nvec, nchunks, st, cfg);
+    case 6: return launch_shape<AR, 6, 4, VI>(k, x, y, nvec, nchunks, st, cfg);
+    default: return launch_shape<AR, 4, 4, VI>(k, x, y, nvec, nchunks, st, cfg);
   }
 }
 

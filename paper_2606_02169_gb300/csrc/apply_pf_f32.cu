@@ -4,6 +4,6 @@
 
 namespace hm {
 
-template cudaError_t launch_apply_pf_t<AR_F32>(const KPlan&, const void*, void*, long long, cudaStream_t, TuneCfg);
+template cudaError_t launch_apply_pf_t<AR_F32, false>(const KPlan&, const void*, void*, long long, cudaStream_t, TuneCfg);
 
 }  // namespace hm

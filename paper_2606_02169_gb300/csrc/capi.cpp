@@ -263,10 +263,11 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
   cfg.pf = (flags >> 12) & 1;
   cfg.scalar = (flags >> 13) & 1;
   cfg.split = (flags >> 14) & 1;
+  cfg.vinv = (flags >> 15) & 1;
   cfg.split_T = (flags >> 16) & 15;
-  if ((cfg.small || cfg.pf || cfg.scalar || cfg.split) && (tile || staged)) {
-    set_error("flag bits 7, 12, 13 and 14 (small low block, prefetching, one right-hand side per element, "
-              "top-site split) apply to the general kernel only");
+  if ((cfg.small || cfg.pf || cfg.scalar || cfg.split || cfg.vinv) && (tile || staged)) {
+    set_error("flag bits 7, 12, 13, 14 and 15 (small low block, prefetching, one right-hand side per element, "
+              "top-site split, one group factor per thread) apply to the general kernel only");
     return HM_ERR_INVALID_ARG;
   }
   if (cfg.split_T && !cfg.split) {
@@ -549,6 +550,14 @@ static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
       if (t < tbest) { tbest = t; best = c; }
     }
   }
+  // the best general-kernel shape with one group factor per thread (a no-op
+  // where the plan's groups do not allow it)
+  if (rc == HM_OK && best.kern == 1) {
+    TuneCfg c = best;
+    c.vinv = 1;
+    const float t = time_cfg(c);
+    if (t < tbest) { tbest = t; best = c; }
+  }
   // the best general-kernel shape again as a top-site split, where the
   // vectors are large enough for one
   if (rc == HM_OK && best.kern == 1 && !best.small && split_top_sites(p, nvec, esize(dtype)) > 0) {
@@ -640,7 +649,8 @@ int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) 
   const TuneCfg c = tuned_cfg(p, dtype, nvec);
   out[0] = c.ctas;
   out[1] = c.s;
-  out[2] = c.mb | (c.small << 1) | (c.pf << 2) | (c.scalar << 3) | (c.split << 4) | (c.split_T << 8);
+  out[2] = c.mb | (c.small << 1) | (c.pf << 2) | (c.scalar << 3) | (c.split << 4) | (c.vinv << 5) |
+           (c.split_T << 8);
   out[3] = c.kern;
   return HM_OK;
 }

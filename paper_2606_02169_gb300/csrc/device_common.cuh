@@ -156,6 +156,7 @@ template <> struct Ar<AR_F32> {
   __device__ static void acc_mul(Acc& a, C v, Acc g) { a = __fmaf_rn(v, g, a); }
   __device__ static TY out(Acc a) { return a; }
   __device__ static TY add_out(TY a, TY b) { return __fadd_rn(a, b); }
+  __device__ static C cmul(C a, C b) { return __fmul_rn(a, b); }
 };
 
 template <> struct Ar<AR_F64> {
@@ -180,6 +181,7 @@ template <> struct Ar<AR_F64> {
   __device__ static void acc_mul(Acc& a, C v, Acc g) { a = __fma_rn(v, g, a); }
   __device__ static TY out(Acc a) { return a; }
   __device__ static TY add_out(TY a, TY b) { return __dadd_rn(a, b); }
+  __device__ static C cmul(C a, C b) { return __dmul_rn(a, b); }
 };
 
 template <> struct Ar<AR_DF64> {
@@ -214,6 +216,16 @@ template <> struct Ar<AR_DF64> {
   }
   __device__ static TY out(Acc a) { return df_to_double(a); }
   __device__ static TY add_out(TY a, TY b) { return __dadd_rn(a, b); }
+  // product of two coefficients as a normalised float pair (Dekker product
+  // with the cross terms, then a fast two-sum): relative error ~2^-46
+  __device__ static C cmul(C a, C b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float t = __fadd_rn(p, e);
+    return make_float2(t, __fsub_rn(e, __fsub_rn(t, p)));
+  }
 };
 
 // Vector policies: TX/TY/Acc hold W right-hand sides of one state; the

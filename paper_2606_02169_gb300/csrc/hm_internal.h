@@ -103,6 +103,9 @@ struct KPlan {
   // flight together; accum = 1 adds the result to y instead of storing it
   int tperm_T;
   int accum;
+  // least common multiple, over the off-diagonal groups, of M_k d_k of the
+  // group's low site k (the period of its digit in states; 0: no group)
+  long long vperiod;
   const KSite* sites;     // [nsites]
   const KChan* ch;
   const KGroup* grp;
@@ -233,6 +236,10 @@ struct TuneCfg {
   // split_T leading sites (0 = chosen from the vector size, split_top_sites)
   int split = 0;
   int split_T = 0;
+  // general kernel: 1 = one v and member coefficients v u per thread where
+  // every factorised group's low digit is the same for the thread's elements
+  // (groups_invariant); rounds differently from 0
+  int vinv = 0;
 };
 
 struct Channel {            // host-side merged channel

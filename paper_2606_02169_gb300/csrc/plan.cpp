@@ -323,6 +323,7 @@ struct HostTables {
   std::vector<int> ell_delta;   // [w*B]
   std::vector<double> ell;      // [w*B]
   int n_hh_diag = 0, n_hh = 0, n_grp_diag = 0, n_grp = 0, ell_w = 0;
+  long long vperiod = 0;        // see KPlan::vperiod
 };
 
 struct HostPlanData {
@@ -463,6 +464,13 @@ static void build_tables(const Plan* p, const std::vector<Channel>& chans, cplx 
   auto add_group = [&](bool diag, const Mixed& m) {
     auto& G = diag ? gd : go;
     auto& GM = diag ? gmem_d : gmem_o;
+    if (!diag) {  // period of the low digit the group's v reads
+      const long long per = p->M[m.lsite] * p->sites[m.lsite].dim;
+      long long a = H.vperiod ? H.vperiod : 1, b = per;
+      while (b) { const long long t = a % b; a = b; b = t; }
+      const long long l = (H.vperiod ? H.vperiod : 1) / a * per;
+      H.vperiod = l > (1LL << 40) ? (1LL << 40) : l;
+    }
     const int dh = p->sites[m.hsite].dim;
     KMember mb{};
     mb.off = diag ? 0 : m.off;
@@ -881,6 +889,7 @@ static int upload_tables(const Plan* p, const HostPlanData& hd, void** dev_out, 
     k.n_grp = H.n_grp;
     k.n_mem = (int)H.mem.size();
     k.ell_w = H.ell_w;
+    k.vperiod = H.vperiod;
     k.nterm_ch = (int)tk.size();
     k.nterms = (int)p->terms.size();
     k.sites = (const KSite*)P(o_sites);

@@ -120,7 +120,7 @@ class Hamiltonian:
 
     def apply_ex(self, x, out=None, native_f64=False, transpose=False, ctas=0, s=0, mb=False, kernel=None,
                  stream=None, presplit=False, small=False, prefetch=False, scalar=False, split=False,
-                 split_sites=0):
+                 split_sites=0, vinv=False):
         """hm_apply with an explicit launch choice. kernel: None or "general"
         (the general kernel), "tile" or "staged". s: rows per iteration of the
         tile kernel (1, 2, 4) or elements per thread of the general one (2, 3,
@@ -129,7 +129,8 @@ class Hamiltonian:
         prefetch: the general kernel with its gathers prefetched by cp.async.
         scalar: one right-hand side per lane (no 2- or 4-wide policy).
         split: top-site split into two passes; split_sites: its number of
-        leading sites (0 = chosen from the vector size).
+        leading sites (0 = chosen from the vector size). vinv: one group
+        factor per lane where the plan allows it.
         presplit (timing diagnostic): x is a float32 tensor of 2 * D *
         nvec (hi, lo) pairs of FP64 values and out a float64 tensor; only the
         double-float apply kernel runs."""
@@ -137,7 +138,7 @@ class Hamiltonian:
         kf = {None: 0, "tile": 8, "general": 16, "staged": 32}[kernel]
         flags = (1 if native_f64 else 0) | (2 if transpose else 0) | (4 if mb else 0) | kf | (int(s) << 8)
         flags |= (128 if small else 0) | (4096 if prefetch else 0) | (8192 if scalar else 0)
-        flags |= (1 << 14 if split else 0) | (int(split_sites) << 16)
+        flags |= (1 << 14 if split else 0) | (1 << 15 if vinv else 0) | (int(split_sites) << 16)
         if presplit:
             if x.dtype != torch.float32 or out is None or out.dtype != torch.float64 or x.numel() != 2 * out.numel():
                 raise ValueError("presplit needs float32 pairs x (2 * D * nvec) and a float64 out")
@@ -209,14 +210,14 @@ class Hamiltonian:
         return self.tuned_config(nvec, dtype)
 
     def tuned_config(self, nvec: int = 1, dtype=torch.float64):
-        """dict(ctas, s, mb, small, prefetch, scalar, split, split_sites, kernel) of the stored launch choice (0 =
+        """dict(ctas, s, mb, small, prefetch, scalar, split, vinv, split_sites, kernel) of the stored launch choice (0 =
         library default; kernel 1 = general, 2 = tile, 3 = staged)."""
         code = _dtype_code(dtype)
         out = (ctypes.c_int32 * 4)()
         C.check(self._lib.hm_tuned_config(self._h, int(nvec), code, out), "hm_tuned_config")
         return {"ctas": out[0], "s": out[1], "mb": out[2] & 1, "small": (out[2] >> 1) & 1,
                 "prefetch": (out[2] >> 2) & 1, "scalar": (out[2] >> 3) & 1, "split": (out[2] >> 4) & 1,
-                "split_sites": (out[2] >> 8) & 15, "kernel": out[3]}
+                "vinv": (out[2] >> 5) & 1, "split_sites": (out[2] >> 8) & 15, "kernel": out[3]}
 
 
 class Batch:

@@ -160,8 +160,12 @@ def sampled_parity(model, dtype, seed, n_random, tol):
     cfg = h.tune(1, tdt)
     x = W.torch_vector(D, seed, dtype=tdt)
     y = h.apply(x)
-    y0 = h.apply_ex(x, kernel={1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]], small=bool(cfg["small"]))
-    # (the prefetching variant sums like the plain general kernel)
+    kernel = {1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]]
+    extra = {} if kernel != "general" else dict(split=bool(cfg["split"]), split_sites=cfg["split_sites"],
+                                                vinv=bool(cfg["vinv"]))
+    y0 = h.apply_ex(x, kernel=kernel, small=bool(cfg["small"]), **extra)
+    # (the prefetching, register-capped, elements-per-thread and lanes-per-
+    # state variants sum like the default launch of the same form)
     torch.cuda.synchronize()
     assert torch.equal(y, y0), f"tuned launch {cfg} differs from the default launch of its kernel"
     del y0

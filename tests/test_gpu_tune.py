@@ -90,7 +90,7 @@ def test_tuned_apply_matches_its_kernel(dtype):
     kernel = {1: "general", 2: "tile", 3: "staged"}[cfg["kernel"]]
     y2 = h.apply_ex(xd, kernel=kernel, s=cfg["s"], mb=bool(cfg["mb"]), ctas=cfg["ctas"], small=bool(cfg["small"]),
                     prefetch=bool(cfg["prefetch"]), scalar=bool(cfg["scalar"]), split=bool(cfg["split"]),
-                    split_sites=cfg["split_sites"])
+                    split_sites=cfg["split_sites"], vinv=bool(cfg["vinv"]))
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
     # a second plan with the same signature takes the cached choice without timing
