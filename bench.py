@@ -160,19 +160,24 @@ def kernel_source_hash():
     # the sources the general apply kernel (plain and prefetching) and the
     # split pass compile from
     for f in ("apply.cu", "apply_kernel.cuh", "apply_launch.cuh", "apply_df64.cu", "apply_f32.cu",
-              "apply_pf_df64.cu", "apply_pf_f32.cu", "device_common.cuh", "plan.cpp", "hm_internal.h"):
+              "apply_pf_df64.cu", "apply_pf_f32.cu", "apply_vi_df64.cu", "apply_vi_f32.cu", "apply_pf_vi_df64.cu",
+              "apply_pf_vi_f32.cu", "device_common.cuh", "plan.cpp", "hm_internal.h"):
         with open(os.path.join(ROOT, "paper_2606_02169_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_profile(key):
+def recorded_profile(key, launch=None):
     """The committed ncu record of one apply (DRAM bytes, thread instructions
-    per launch), or None if the kernel sources changed since it was taken."""
+    per launch), or None if the kernel sources changed since it was taken or
+    it was taken on another launch variant than `launch` (a tuned_config)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         rec = t.get(key)
+        if rec and launch is not None and rec.get("launch"):
+            if any(int(launch.get(k, 0)) != int(v) for k, v in rec["launch"].items()):
+                return None
         if rec and rec.get("source_hash") == kernel_source_hash():
             return rec
     except Exception:
@@ -180,8 +185,8 @@ def recorded_profile(key):
     return None
 
 
-def recorded_traffic(key):
-    rec = recorded_profile(key)
+def recorded_traffic(key, launch=None):
+    rec = recorded_profile(key, launch)
     return rec["dram_bytes_per_launch"] if rec else None
 
 
@@ -288,44 +293,51 @@ def timed(fn, steps, warmup, ws, stream):
 
 def e2e_pipelined(h, x, s_c, steps, ws, warmup=3):
     """Total ms of `steps` end-to-end applies (pinned host x -> device, hm_apply,
-    y -> pinned host), pipelined over copy-in / compute / copy-out streams with
-    two device buffers; barrier + synchronize on both sides, max over ranks."""
+    y -> pinned host) with two device buffers: the copies in both directions
+    share one stream (on this host, copies in both directions at once ran at
+    about a quarter of the one-way rate each), the applies run on s_c and
+    overlap them; barrier + synchronize on both sides, max over ranks."""
     import torch
     xh = x.cpu().pin_memory()
     yh = [torch.empty_like(xh).pin_memory() for _ in range(2)]
     xd = [torch.empty_like(x) for _ in range(2)]
     yd = [torch.empty_like(x) for _ in range(2)]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    s_io = torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_c = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def copy_out(i):
+        b = i & 1
+        s_io.wait_event(ev_c[b])              # the apply of step i wrote yd[b]
+        with torch.cuda.stream(s_io):
+            yh[b].copy_(yd[b], non_blocking=True)
+        ev_out[b].record(s_io)
 
     def run(k):
         for i in range(k):
             b = i & 1
             if i >= 2:
-                s_in.wait_event(ev_c[b])      # the apply of step i-2 has read xd[b]
-            with torch.cuda.stream(s_in):
+                s_io.wait_event(ev_c[b])      # the apply of step i-2 has read xd[b]
+            with torch.cuda.stream(s_io):
                 xd[b].copy_(xh, non_blocking=True)
-            ev_in[b].record(s_in)
+            ev_in[b].record(s_io)
+            if i >= 1:
+                copy_out(i - 1)               # queued behind the next copy-in
             s_c.wait_event(ev_in[b])
             if i >= 2:
                 s_c.wait_event(ev_out[b])     # the copy-out of step i-2 has read yd[b]
             h.apply(xd[b], out=yd[b], stream=s_c)
             ev_c[b].record(s_c)
-            s_out.wait_event(ev_c[b])
-            with torch.cuda.stream(s_out):
-                yh[b].copy_(yd[b], non_blocking=True)
-            ev_out[b].record(s_out)
+        copy_out(k - 1)
 
     run(warmup)
     torch.cuda.synchronize()
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s_in)
+    e0.record(s_io)
     run(steps)
-    s_out.wait_event(ev_c[(steps - 1) & 1])
-    e1.record(s_out)
+    e1.record(s_io)
     torch.cuda.synchronize()
     barrier(ws)
     ms = max_over_ranks(e0.elapsed_time(e1), ws)
@@ -486,7 +498,7 @@ def run_ours(args):
     # the dominant kernel alone: the double-float apply on pre-split input
     ms_kernel = kernel_only_ms(h, x, y, tuned, max(5, min(args.steps, 50)), stream)
     achieved = bytes_alg / (ms_kernel * 1e-3) / 1e9
-    traffic = recorded_traffic("apply_f64_" + WORKLOAD)
+    traffic = recorded_traffic("apply_f64_" + WORKLOAD, tuned)
 
     # end to end through the public API, run the way a caller streaming vectors
     # through the GPU would: every step copies its x from pinned host memory
@@ -506,8 +518,9 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU", "tuned_launch": tuned},
         "e2e": {"value": e2e_val, "unit": "Gstates/s", "h2d_bytes_per_step": 8 * D,
                 "d2h_bytes_per_step": 8 * D, "steps": k_e2e,
-                "how": "pinned host x -> device, hm_apply, y -> pinned host every step; copy-in, apply and "
-                       "copy-out on three streams with two device buffers (steps overlap)"},
+                "how": "pinned host x -> device, hm_apply, y -> pinned host every step; copies in both "
+                       "directions on one stream, applies on another, two device buffers (copies overlap "
+                       "the applies)"},
         # per FP64 step: k_split_f64 (split + range check), the double-float
         # apply, and the native FP64 fallback launch that returns at once
         # unless the split flagged x
@@ -524,7 +537,7 @@ def run_ours(args):
     # issue / FP32-pipe view of the same kernel: thread instructions per state
     # (ncu) times the measured rate, against 4 schedulers x 32 lanes per SM at
     # the sampled clock
-    rec = recorded_profile("apply_f64_" + WORKLOAD)
+    rec = recorded_profile("apply_f64_" + WORKLOAD, tuned)
     if rec and rec.get("thread_inst_per_launch"):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
