@@ -13,7 +13,8 @@
  *     y_F = <F|H|x> = sum over channels of coef * Lambda * Lambda * x_{F+offset}
  *   (Sec. II, Sec. IV.B Eq. sourceoffset, App. A).
  *
- * Vectors: caller-owned DEVICE pointers, state-major interleaved: element v
+ * Vectors: caller-owned DEVICE pointers (hm_apply also takes page-locked
+ * host memory, see there), state-major interleaved: element v
  * of state k is at [k*nvec + v]. Real storage (HM_F64 / HM_F32) or complex
  * storage (HM_C128 / HM_C64: each element an interleaved (re, im) pair, the
  * layout of C99 double/float _Complex). For a real H the real and imaginary
@@ -139,8 +140,13 @@ int hm_set_coefficients(hm_handle h, const double* coefs);
 int64_t hm_dim(hm_handle h);
 int32_t hm_num_terms(hm_handle h);
 
-/* y = H x for nvec right-hand sides (x, y: device, D*nvec elements of dtype;
- * x read-only, y fully overwritten; x and y must not overlap). Each output
+/* y = H x for nvec right-hand sides (x, y: D*nvec elements of dtype in
+ * device memory or in page-locked host memory registered with CUDA --
+ * cudaHostAlloc / cudaHostRegister -- which the kernels reach over the
+ * CPU-GPU link: FP64 x is read once by the split pass, FP32 x is copied once
+ * into device scratch, y is written once; plain pageable host memory gives
+ * HM_ERR_INVALID_ARG; x read-only, y fully overwritten; x and y must not
+ * overlap). Each output
  * element is owned by exactly one GPU lane (pull form, Sec. II): no atomics,
  * bit-reproducible run to run. HM_F64 first splits x into D*nvec float
  * pairs of stream-ordered scratch from a library memory pool per device,

@@ -204,6 +204,30 @@ static cudaError_t launch_general(const KPlan& k, const void* x, void* y, long l
   return general_t<AR_DF64, false>(k, x, y, nvec, s, c);
 }
 
+// Page-locked host memory (reached by kernels over the CPU-GPU link)?
+bool host_resident(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// dst = src, n 4-byte words, one pass (src may be pinned host memory); V4:
+// src and dst 16-byte aligned, 16-byte accesses for all but the tail
+template <bool V4>
+__global__ void k_copy_words(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, long long n) {
+  const long long n4 = V4 ? n / 4 : 0;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if constexpr (V4) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (long long i = t0; i < n4; i += st) d4[i] = s4[i];
+  }
+  for (long long i = 4 * n4 + t0; i < n; i += st) dst[i] = src[i];
+}
+
 // y = H x (or H^T x) on stream s. Kernels: cfg.kern = 0 or 1 the general
 // kernel (on the plan's low block, or with cfg.small on the small one), 2 the
 // tile kernel, 3 the staged kernel (autotuner candidates). A strict request
@@ -211,6 +235,31 @@ static cudaError_t launch_general(const KPlan& k, const void* x, void* y, long l
 int apply_on(Plan* p, bool transpose, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
              TuneCfg cfg, bool native_f64) {
   if (p->sector) return launch_sector(p, x, y, nvec, dt, s);  // the Lanczos driver on a sector plan
+  // vectors in pinned host memory: FP64 x is read once by the split pass
+  // below; FP32 x is first copied once into device scratch (the kernels read
+  // each element once per hop); y is written once by the kernel. The split
+  // into two passes (whose second pass reads y back) is not used for host y.
+  Scratch xstage;
+  if (dt == HM_F32 && host_resident(x)) {
+    const long long n = vec_states(p) * nvec;
+    int rc = scratch_alloc(xstage, (size_t)n * 4, s);
+    if (rc) return rc;
+    const long long grid = std::max<long long>(1, std::min<long long>((n / 4 + 255) / 256, (long long)num_sms() * 8));
+    if (((uintptr_t)x % 16) == 0)
+      k_copy_words<true><<<(unsigned)grid, 256, 0, s>>>((const uint32_t*)x, (uint32_t*)xstage.ptr, n);
+    else
+      k_copy_words<false><<<(unsigned)grid, 256, 0, s>>>((const uint32_t*)x, (uint32_t*)xstage.ptr, n);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return cuda_fail(e0, "host x staging");
+    x = xstage.ptr;
+  }
+  if (cfg.split && host_resident(y)) {
+    if (cfg.strict) {
+      set_error("the top-site split reads y back: not for y in host memory");
+      return HM_ERR_UNSUPPORTED;
+    }
+    cfg.split = 0;
+  }
   const KPlan& k = transpose ? p->kt : p->k;
   const StreamSet* ss = cfg.kern == 3 ? get_stream(p, nvec, s) : nullptr;
   // the general kernel on the small low block (the staged kernel's tables)

@@ -58,6 +58,17 @@ int check_vec_args(const Plan* p, const void* x, const void* y, long long nvec, 
     return HM_ERR_INVALID_ARG;
   }
   if ((double)vec_states(p) * (double)nvec > 9.0e18) { set_error("D * nvec overflows int64"); return HM_ERR_OVERFLOW; }
+  // device memory, managed memory or page-locked host memory registered with
+  // CUDA (kernels reach it through the unified address space); plain
+  // pageable host memory is not accepted
+  for (const void* v : {x, y}) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, v) != cudaSuccess || a.type == cudaMemoryTypeUnregistered) {
+      cudaGetLastError();
+      set_error("vectors must be device memory or page-locked (pinned) host memory");
+      return HM_ERR_INVALID_ARG;
+    }
+  }
   if (overlap(x, y, (size_t)(vec_states(p) * nvec) * esize(dt))) {
     set_error("x and y overlap (the pull form needs x read-only while y is written)");
     return HM_ERR_ALIAS;

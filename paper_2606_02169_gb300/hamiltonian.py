@@ -27,9 +27,9 @@ def _dtype_code(t) -> int:
     return _CODES[dt]
 
 
-def _check_vec(t: torch.Tensor, name: str):
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+def _check_vec(t: torch.Tensor, name: str, host_ok: bool = False):
+    if not t.is_cuda and not (host_ok and t.device.type == "cpu" and t.is_pinned()):
+        raise ValueError(f"{name} must be a CUDA tensor" + (" or a pinned CPU tensor" if host_ok else ""))
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
 
@@ -110,10 +110,15 @@ class Hamiltonian:
         return x.numel() // self.D
 
     def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        """y = H x for x of D*nvec elements (state-major, x[k*nvec + v])."""
-        _check_vec(x, "x")
-        y = torch.empty_like(x) if out is None else out
-        _check_vec(y, "out")
+        """y = H x for x of D*nvec elements (state-major, x[k*nvec + v]).
+        x and out may be CUDA tensors or pinned CPU tensors (the library then
+        reads x and writes y over the CPU-GPU link inside the call)."""
+        _check_vec(x, "x", host_ok=True)
+        if out is None:
+            y = torch.empty_like(x) if x.is_cuda else torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        else:
+            y = out
+        _check_vec(y, "out", host_ok=True)
         C.check(self._lib.hm_apply(self._h, x.data_ptr(), y.data_ptr(), self._nvec(x), _dtype_code(x),
                                    _stream(stream)), "hm_apply")
         return y
