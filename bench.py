@@ -695,7 +695,8 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     xs_ = W.torch_vector(hs.D, 21, dtype=torch.float64)
     ys_ = torch.empty_like(xs_)
     k = 5
-    ms_s = timed(lambda: hs.apply(xs_, out=ys_), k, 2, 1, stream) / k
+    ms_s = timed(lambda: hs.apply(xs_, out=ys_), k, 2, 1, stream) / k          # block form
+    ms_r = timed(lambda: hs.apply_ex(xs_, out=ys_, kernel="rows"), k, 2, 1, stream) / k   # per-row kernel
     import oracle
     rows = np.arange(2000) * (hs.D // 2000)
     xh = xs_.cpu().numpy()
@@ -712,6 +713,7 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     ms_f = timed(lambda: hf.apply(xf_, out=yf_), k, 2, 1, stream) / k
     out["sector_chain_n30_m0_f64"] = {
         "Dsec": math.comb(ns, ns // 2), "ms": ms_s, "gstates_s": math.comb(ns, ns // 2) / ms_s / 1e6,
+        "ms_per_row_kernel": ms_r,
         "hbm_frac_algorithmic": 16 * math.comb(ns, ns // 2) / ms_s / 1e6 / hbm,
         "full_basis_ms": ms_f, "full_basis_gstates_s": hf.D / ms_f / 1e6,
         "vector_bytes_sector_vs_full": math.comb(ns, ns // 2) / hf.D,

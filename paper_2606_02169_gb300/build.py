@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhm.so")
 SOURCES = ["capi.cpp", "plan.cpp", "tile_plan.cpp", "apply.cu", "apply_f32.cu", "apply_df64.cu", "apply_f64.cu",
-           "tile_f32.cu", "tile_df64.cu", "adjoint.cu", "lanczos.cu", "grad_static.cu", "sector.cu",
+           "tile_f32.cu", "tile_df64.cu", "adjoint.cu", "lanczos.cu", "grad_static.cu", "sector.cu", "sector_blk.cu",
            "stream_f32.cu", "stream_df64.cu", "stream_f64.cu", "apply_pf_f32.cu", "apply_pf_df64.cu",
            "apply_pf_f64.cu", "apply_v2_f32.cu", "apply_v4_f32.cu", "apply_v_df64.cu",
            "apply_batch_f32.cu", "apply_batch_df64.cu", "apply_vi_df64.cu", "apply_vi_f32.cu",

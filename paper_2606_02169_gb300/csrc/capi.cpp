@@ -252,7 +252,13 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
   real_view(dtype, nvec);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
-  if ((rc = no_sector(p, "hm_apply_ex"))) return rc;
+  if (p->sector) {  // sector plans: bit 4 selects the per-row kernel, nothing else applies
+    if (flags & ~16) {
+      set_error("hm_apply_ex on a sector plan takes flag bit 4 (the per-row kernel) only");
+      return HM_ERR_UNSUPPORTED;
+    }
+    return launch_sector(p, x, y, nvec, dtype, (cudaStream_t)stream, (flags & 16) != 0);
+  }
   if ((rc = complex_only(p, "hm_apply_ex"))) return rc;
   TuneCfg cfg;
   cfg.ctas = ctas > 0 ? ctas : 0;
@@ -571,13 +577,19 @@ static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream) {
   }
   // the best general-kernel shape again as a top-site split, where the
   // vectors are large enough for one
-  if (rc == HM_OK && best.kern == 1 && !best.small && split_top_sites(p, nvec, esize(dtype)) > 0) {
-    TuneCfg c = best;
-    c.split = 1;
-    c.strict = 1;
-    const float t = time_cfg(c);
-    if (rc == HM_ERR_UNSUPPORTED) rc = HM_OK;
-    else if (t < tbest) { tbest = t; best = c; }
+  const int T0 = split_top_sites(p, nvec, esize(dtype));
+  if (rc == HM_OK && best.kern == 1 && !best.small && T0 > 0) {
+    const TuneCfg base = best;
+    for (int T : {T0 - 1, T0, T0 + 1}) {  // the best T sits near the 32 MiB rule
+      if (T < 1 || T >= p->N || rc != HM_OK) continue;
+      TuneCfg c = base;
+      c.split = 1;
+      c.split_T = T;
+      c.strict = 1;
+      const float t = time_cfg(c);
+      if (rc == HM_ERR_UNSUPPORTED) rc = HM_OK;
+      else if (t < tbest) { tbest = t; best = c; }
+    }
   }
   // nvec even: the calls above ran 2 or 4 right-hand sides per lane; one per
   // lane (bit-identical) is a candidate too

@@ -292,6 +292,10 @@ struct Plan {
   long long Dsec = 0;
   KSector ksec{};
   void* sec_dev = nullptr;
+  // block form of the sector apply (sector_blk.cu), when the plan fits it
+  KSecBlk ksb{};
+  void* secb_dev = nullptr;
+  bool secb_ok = false;
   long long sec_nA = 0, sec_ntab = 0;   // rank-table and coefficient-pool lengths
   long long sec_ndl = 0;                // rank-delta pool length
   bool sec_needA = true;                // some channel updates ranks from the rank tables
@@ -342,7 +346,13 @@ int split_top_sites(const Plan* p, long long nvec, size_t es);
 int build_sector(Plan* p);   // sector tables from p->chH (after build_plan's host half)
 void free_sector(Plan* p);
 std::string export_sector_json(const Plan* p, long long digit_total, int* rc);
-int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
+int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+                  bool rows = false);
+// sector_blk.cu: block-form tables (none when the plan does not fit them)
+// and its launch on x already split into float pairs for FP64 storage
+int build_sector_blk(Plan* p);
+void free_sector_blk(Plan* p);
+cudaError_t launch_sector_blk(const Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
 // length of the plan's vectors in states: D, or Dsec for a sector plan
 inline long long vec_states(const Plan* p) { return p->sector ? p->Dsec : p->D; }
 

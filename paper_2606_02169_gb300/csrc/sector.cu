@@ -227,6 +227,7 @@ void free_sector(Plan* p) {
   if (p->sec_dev) cudaFree(p->sec_dev);
   p->sec_dev = nullptr;
   p->ksec = KSector{};
+  free_sector_blk(p);
 }
 
 // Host half of a sector plan: counts, rank tables, channels, rank-delta
@@ -523,7 +524,7 @@ int build_sector(Plan* p) {
   p->sec_ntab = (long long)h.tab.size();
   p->sec_ndl = (long long)h.dl.size();
   p->sec_needA = h.needA;
-  return HM_OK;
+  return build_sector_blk(p);
 }
 
 // The host tables of the sector plan with digit total Kl as JSON text.
@@ -589,16 +590,18 @@ static cudaError_t sector_launch(Plan* p, const void* x, void* y, long long nvec
   return p->ksec.wide ? sector_launch<AR, long long>(p, x, y, nvec, s) : sector_launch<AR, int>(p, x, y, nvec, s);
 }
 
-int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
+// The block form where the plan has it (rows = false), else the per-row kernel.
+int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s, bool rows) {
+  const bool blk = p->secb_ok && !rows;
   cudaError_t e;
   if (dt == HM_F32) {
-    e = sector_launch<AR_F32>(p, x, y, nvec, s);
+    e = blk ? launch_sector_blk(p, x, y, nvec, dt, s) : sector_launch<AR_F32>(p, x, y, nvec, s);
   } else {  // FP64: split into float pairs first
     const float2* xs = nullptr;
     Scratch xsb;
     int rc = split_vector(x, p->Dsec * nvec, s, xsb, &xs);
     if (rc) return rc;
-    e = sector_launch<AR_DF64>(p, xs, y, nvec, s);
+    e = blk ? launch_sector_blk(p, xs, y, nvec, dt, s) : sector_launch<AR_DF64>(p, xs, y, nvec, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "sector apply launch");
   return HM_OK;

@@ -54,4 +54,45 @@ struct KSector {
   long long nlt;           // its length
 };
 
+enum { SB_PDIAG = 0, SB_MDIAG = 1, SB_PMOVE = 2, SB_MMOVE = 3 };
+
+struct KSBChan {
+  int kind;
+  int tab;         // coefficient table base, entry [n_si * dj + n_sj] (target digits)
+  int dj;
+  int si, sj;      // sites (sj = -1: single-site)
+  int pfx;         // SB_M*: 0 if si is the prefix site, 1 if sj is
+  int qp;          // SB_PMOVE: unused; SB_MMOVE: move of the prefix digit (source = target - qp)
+  int xr;          // SB_MMOVE: index of its source-rank table
+  long long dblk;  // moves: source block = block - dblk
+  int lbit, lwid;  // SB_M*: packed-digit field of the suffix site
+};
+
+// Block form (sector_blk.cu): prefix blocks of contiguous packed states,
+// per-suffix tables. Channels in kind order: [0, n0) SB_PDIAG, [n0, n1)
+// SB_PMOVE, [n1, n2) SB_MDIAG, [n2, nch) SB_MMOVE.
+struct KSecBlk {
+  long long nvb;           // blocks with retained states
+  int h, K, nch, w, G;
+  int n0, n1, n2;
+  const long long* start;  // [prefix tuples] packed index of the block's first state
+  const int* vb;           // [nvb] those blocks, ascending
+  const long long* mp;     // [h] prefix multipliers (block units)
+  const int* pdim;         // [h] prefix site dimensions
+  const int* off;          // [K + 2] suffix-sector offsets (positions g)
+  const uint32_t* sdig;    // [G] packed suffix digits
+  const KSBChan* ch;       // [nch]
+  const double* tab_d;
+  const float2* tab_df;
+  const float* tab_f;
+  const double* dS_d;      // [G] suffix-only diagonal (+ constant)
+  const float2* dS_df;
+  const float* dS_f;
+  const int* ell_r;        // [w * G] source rank - target rank (same sector)
+  const double* ell_d;     // [w * G] coefficients
+  const float2* ell_df;
+  const float* ell_f;
+  const int* xr;           // [nxr * G] source ranks of coupled moves
+};
+
 }  // namespace hm

@@ -127,7 +127,8 @@ class Hamiltonian:
                  stream=None, presplit=False, small=False, prefetch=False, scalar=False, split=False,
                  split_sites=0, vinv=False):
         """hm_apply with an explicit launch choice. kernel: None or "general"
-        (the general kernel), "tile" or "staged". s: rows per iteration of the
+        (the general kernel), "tile" or "staged"; on a sector plan None (the
+        block form where the plan has it) or "rows" (the per-row kernel). s: rows per iteration of the
         tile kernel (1, 2, 4) or elements per thread of the general one (2, 3,
         4, 6, 8); 0 = default. mb: register-capped general kernel. ctas: grid
         size. small: the general kernel on the small low block (tables in L1).
@@ -140,7 +141,7 @@ class Hamiltonian:
         nvec (hi, lo) pairs of FP64 values and out a float64 tensor; only the
         double-float apply kernel runs."""
         _check_vec(x, "x")
-        kf = {None: 0, "tile": 8, "general": 16, "staged": 32}[kernel]
+        kf = {None: 0, "tile": 8, "general": 16, "rows": 16, "staged": 32}[kernel]
         flags = (1 if native_f64 else 0) | (2 if transpose else 0) | (4 if mb else 0) | kf | (int(s) << 8)
         flags |= (128 if small else 0) | (4096 if prefetch else 0) | (8192 if scalar else 0)
         flags |= (1 << 14 if split else 0) | (1 << 15 if vinv else 0) | (int(split_sites) << 16)

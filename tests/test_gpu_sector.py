@@ -178,7 +178,8 @@ def test_sector_errors():
     assert e.value.code == C.HM_ERR_INVALID_ARG
     h = _ham(sites, [(0, "Sp", 1, "Sm", 1.0), (0, "Sm", 1, "Sp", 1.0)], 2)
     x = torch.zeros(h.D, dtype=torch.float64, device="cuda")
-    for call in (lambda: h.apply_ex(x), lambda: h.adjoint(x, x), lambda: h.tune(1, torch.float64),
+    for call in (lambda: h.apply_ex(x, kernel="tile"), lambda: h.apply_ex(x, mb=True), lambda: h.adjoint(x, x),
+                 lambda: h.tune(1, torch.float64),
                  lambda: _ham(sites, [(0, "Sp", 1, "Sm", 1.0)], 2).adjoint(x, want_gcoef=False)):
         with pytest.raises(HmError) as e:
             call()
