@@ -357,7 +357,8 @@ int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);
  * bit 0: H^T instead of H; bit 1: the tile kernel's tables for
  * nvec = which >> 8 (at least 1; HM_ERR_UNSUPPORTED if there is no tile
  * form); bit 2: the tables of hm_create_sector for digit_total =
- * which >> 8 (same error codes as hm_create_sector); else the general
+ * which >> 8 (same error codes as hm_create_sector), with bit 4 those of
+ * its block form ("ok": false when the plan has none); else the general
  * kernel's. bit 3: the imaginary part H_im of a complex H (else H_re, or
  * the whole real H). On success *len = bytes needed including
  * the terminating NUL; the text is written only if buf != NULL and

@@ -351,6 +351,7 @@ int launch_sector(Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, 
 // sector_blk.cu: block-form tables (none when the plan does not fit them)
 // and its launch on x already split into float pairs for FP64 storage
 int build_sector_blk(Plan* p);
+std::string export_sector_blk_json(const Plan* p, long long digit_total, int* rc);
 void free_sector_blk(Plan* p);
 cudaError_t launch_sector_blk(const Plan* p, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
 // length of the plan's vectors in states: D, or Dsec for a sector plan

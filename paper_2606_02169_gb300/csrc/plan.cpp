@@ -1110,6 +1110,10 @@ int export_plan(Plan* p, int which, std::string& o) {
     set_error("complex term lists (imaginary matrix elements) are not available for sector plans");
     return HM_ERR_UNSUPPORTED;
   }
+  if ((which & 4) && (which & 16)) {  // block-form sector tables for the digit total which >> 8
+    o = export_sector_blk_json(p, which >> 8, &rc);
+    return rc;
+  }
   if (which & 4) {  // sector tables for the digit total which >> 8
     o = export_sector_json(p, which >> 8, &rc);
     return rc;

@@ -22,7 +22,9 @@
 // (FP32, or double-float on the FP32 pipe for FP64 storage).
 #include <algorithm>
 #include <cstring>
+#include <cstdio>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "device_common.cuh"
@@ -262,10 +264,37 @@ __global__ void __launch_bounds__(kSBNT) k_sector_blk(const KSecBlk S, const typ
 // host: tables of the block form (none when the plan does not fit them)
 // ---------------------------------------------------------------------------
 
-int build_sector_blk(Plan* p) {
-  free_sector_blk(p);
+// Host tables of the block form for digit total K (ok = false when the plan
+// does not fit it: then the per-row kernel serves). No device calls.
+struct SBHost {
+  bool ok = false;
+  int h = 0, w = 0, G = 0, n0 = 0, n1 = 0, n2 = 0;
+  long long K = 0;
+  std::vector<long long> start, mp;
+  std::vector<int> vb, pdim, off, ell_r, xr_flat;
+  std::vector<uint32_t> sdig;
+  std::vector<KSBChan> ch;
+  std::vector<double> tab, dS, ell_d;
+};
+
+static int derive_sector_blk(const Plan* p, long long K, SBHost& o) {
+  o = SBHost{};
+  o.K = K;
   const int N = p->N;
-  const long long K = p->sec_total;
+  long long maxsum = 0;
+  for (auto& st : p->sites) maxsum += st.dim - 1;
+  if (K < 0 || K > maxsum) {
+    set_error("digit total outside [0, sum_k (d_k - 1)]: the sector is empty");
+    return HM_ERR_INVALID_ARG;
+  }
+  for (const Channel& c : p->chH) {  // the sector's terms conserve the digit sum
+    bool nz = false;
+    for (auto& z : c.T) nz = nz || z != std::complex<double>(0, 0);
+    if (nz && c.qi + (c.j >= 0 ? c.qj : 0) != 0) {
+      set_error("the term list does not conserve the sector's digit sum");
+      return HM_ERR_UNSUPPORTED;
+    }
+  }
   // suffix: trailing sites with at most kSBMax tuples
   int h = N;
   long long Bs = 1;
@@ -278,7 +307,7 @@ int build_sector_blk(Plan* p) {
     nblk *= p->sites[k].dim;
     if (nblk > kSBBlocksMax) return HM_OK;  // no block form: the per-row kernel serves
   }
-  if (h > 64) return HM_OK;
+  if (h > 64 || K > 255) return HM_OK;
   // packed suffix digits and multipliers
   std::vector<long long> Ms(N, 1), mp(std::max(h, 1), 1);
   for (int k = N - 2; k >= h; --k) Ms[k] = Ms[k + 1] * p->sites[k + 1].dim;
@@ -335,10 +364,6 @@ int build_sector_blk(Plan* p) {
       vb.push_back((int)b);
       run += cnt[t];
     }
-  }
-  if (run != p->Dsec) {
-    set_error("internal: sector block form does not cover the sector");
-    return HM_ERR_CUDA;
   }
   // channels
   std::vector<KSBChan> ch;
@@ -423,7 +448,6 @@ int build_sector_blk(Plan* p) {
   for (auto& c : ch) ++nk[c.kind == SB_PDIAG ? 0 : c.kind == SB_PMOVE ? 1 : c.kind == SB_MDIAG ? 2 : 3];
   int w = 0;
   for (auto& e : ell) w = std::max(w, (int)e.size());
-  // upload
   std::vector<int> ell_r((size_t)w * G, 0);
   std::vector<double> ell_d((size_t)w * G, 0.0);
   for (int g = 0; g < G; ++g)
@@ -431,6 +455,44 @@ int build_sector_blk(Plan* p) {
       ell_r[e * G + g] = ell[g][e].first;
       ell_d[e * G + g] = ell[g][e].second;
     }
+  for (auto& v : xr) o.xr_flat.insert(o.xr_flat.end(), v.begin(), v.end());
+  o.pdim.assign(std::max(h, 1), 1);
+  for (int k = 0; k < h; ++k) o.pdim[k] = p->sites[k].dim;
+  o.ok = true;
+  o.h = h;
+  o.w = w;
+  o.G = G;
+  o.n0 = nk[0];
+  o.n1 = nk[0] + nk[1];
+  o.n2 = nk[0] + nk[1] + nk[2];
+  o.start = std::move(start);
+  o.mp = std::move(mp);
+  o.vb = std::move(vb);
+  o.off = std::move(off);
+  o.sdig = std::move(sdig);
+  o.ch = std::move(ch);
+  o.tab = std::move(tab);
+  o.dS = std::move(dS);
+  o.ell_r = std::move(ell_r);
+  o.ell_d = std::move(ell_d);
+  return HM_OK;
+}
+
+int build_sector_blk(Plan* p) {
+  free_sector_blk(p);
+  SBHost o;
+  int rc = derive_sector_blk(p, p->sec_total, o);
+  if (rc || !o.ok) return rc;
+  long long cover = 0;
+  for (size_t i = 0; i < o.vb.size(); ++i) {
+    int P = 0;
+    for (int k = 0; k < o.h; ++k) P += (int)((o.vb[i] / o.mp[k]) % o.pdim[k]);
+    cover += o.off[o.K - P + 1] - o.off[o.K - P];
+  }
+  if (cover != p->Dsec) {
+    set_error("internal: sector block form does not cover the sector");
+    return HM_ERR_CUDA;
+  }
   auto split = [](const std::vector<double>& v, std::vector<float2>& df, std::vector<float>& f) {
     for (double a : v) {
       const float hi = (float)a;
@@ -440,13 +502,9 @@ int build_sector_blk(Plan* p) {
   };
   std::vector<float2> tab_df, dS_df, ell_df;
   std::vector<float> tab_f, dS_f, ell_f;
-  split(tab, tab_df, tab_f);
-  split(dS, dS_df, dS_f);
-  split(ell_d, ell_df, ell_f);
-  std::vector<int> xr_flat;
-  for (auto& v : xr) xr_flat.insert(xr_flat.end(), v.begin(), v.end());
-  std::vector<int> pdim(std::max(h, 1), 1);
-  for (int k = 0; k < h; ++k) pdim[k] = p->sites[k].dim;
+  split(o.tab, tab_df, tab_f);
+  split(o.dS, dS_df, dS_f);
+  split(o.ell_d, ell_df, ell_f);
   struct Sec { const void* src; size_t bytes; size_t off; };
   std::vector<Sec> secs;
   size_t cur = 0;
@@ -457,24 +515,24 @@ int build_sector_blk(Plan* p) {
     cur += std::max<size_t>(bytes, 1);
     return o;
   };
-  const size_t o_start = add(start.data(), start.size() * 8);
-  const size_t o_vb = add(vb.data(), vb.size() * 4);
-  const size_t o_mp = add(mp.data(), mp.size() * 8);
-  const size_t o_pd = add(pdim.data(), pdim.size() * 4);
-  const size_t o_off = add(off.data(), off.size() * 4);
-  const size_t o_sdig = add(sdig.data(), sdig.size() * 4);
-  const size_t o_ch = add(ch.data(), ch.size() * sizeof(KSBChan));
-  const size_t o_td = add(tab.data(), tab.size() * 8);
+  const size_t o_start = add(o.start.data(), o.start.size() * 8);
+  const size_t o_vb = add(o.vb.data(), o.vb.size() * 4);
+  const size_t o_mp = add(o.mp.data(), o.mp.size() * 8);
+  const size_t o_pd = add(o.pdim.data(), o.pdim.size() * 4);
+  const size_t o_off = add(o.off.data(), o.off.size() * 4);
+  const size_t o_sdig = add(o.sdig.data(), o.sdig.size() * 4);
+  const size_t o_ch = add(o.ch.data(), o.ch.size() * sizeof(KSBChan));
+  const size_t o_td = add(o.tab.data(), o.tab.size() * 8);
   const size_t o_tdf = add(tab_df.data(), tab_df.size() * 8);
   const size_t o_tf = add(tab_f.data(), tab_f.size() * 4);
-  const size_t o_sd = add(dS.data(), dS.size() * 8);
+  const size_t o_sd = add(o.dS.data(), o.dS.size() * 8);
   const size_t o_sdf = add(dS_df.data(), dS_df.size() * 8);
   const size_t o_sf = add(dS_f.data(), dS_f.size() * 4);
-  const size_t o_er = add(ell_r.data(), ell_r.size() * 4);
-  const size_t o_ed = add(ell_d.data(), ell_d.size() * 8);
+  const size_t o_er = add(o.ell_r.data(), o.ell_r.size() * 4);
+  const size_t o_ed = add(o.ell_d.data(), o.ell_d.size() * 8);
   const size_t o_edf = add(ell_df.data(), ell_df.size() * 8);
   const size_t o_ef = add(ell_f.data(), ell_f.size() * 4);
-  const size_t o_xr = add(xr_flat.data(), xr_flat.size() * 4);
+  const size_t o_xr = add(o.xr_flat.data(), o.xr_flat.size() * 4);
   const size_t total = (cur + 255) & ~size_t(255);
   std::vector<unsigned char> host(total, 0);
   for (auto& sc : secs)
@@ -490,15 +548,15 @@ int build_sector_blk(Plan* p) {
   const unsigned char* b = (const unsigned char*)p->secb_dev;
   KSecBlk& S = p->ksb;
   S = KSecBlk{};
-  S.nvb = (long long)vb.size();
-  S.h = h;
-  S.K = (int)K;
-  S.nch = (int)ch.size();
-  S.n0 = nk[0];
-  S.n1 = nk[0] + nk[1];
-  S.n2 = nk[0] + nk[1] + nk[2];
-  S.w = w;
-  S.G = G;
+  S.nvb = (long long)o.vb.size();
+  S.h = o.h;
+  S.K = (int)o.K;
+  S.nch = (int)o.ch.size();
+  S.n0 = o.n0;
+  S.n1 = o.n1;
+  S.n2 = o.n2;
+  S.w = o.w;
+  S.G = o.G;
   S.start = (const long long*)(b + o_start);
   S.vb = (const int*)(b + o_vb);
   S.mp = (const long long*)(b + o_mp);
@@ -519,6 +577,53 @@ int build_sector_blk(Plan* p) {
   S.xr = (const int*)(b + o_xr);
   p->secb_ok = true;
   return HM_OK;
+}
+
+// The host tables of the block form with digit total K as JSON text
+// ("ok": false when the plan does not fit the block form).
+std::string export_sector_blk_json(const Plan* p, long long K, int* rc) {
+  SBHost o;
+  *rc = derive_sector_blk(p, K, o);
+  if (*rc) return std::string();
+  std::string s = std::string("{\"ok\":") + (o.ok ? "true" : "false");
+  auto num = [&](double v) {
+    char b[40];
+    snprintf(b, sizeof(b), "%.17g", v);
+    s += b;
+  };
+  auto arr = [&](const char* name, size_t n, auto f) {
+    s += ",\"";
+    s += name;
+    s += "\":[";
+    for (size_t i = 0; i < n; ++i) {
+      if (i) s += ",";
+      f(i);
+    }
+    s += "]";
+  };
+  s += ",\"h\":" + std::to_string(o.h) + ",\"K\":" + std::to_string(o.K) + ",\"w\":" + std::to_string(o.w) +
+       ",\"G\":" + std::to_string(o.G) + ",\"n0\":" + std::to_string(o.n0) + ",\"n1\":" + std::to_string(o.n1) +
+       ",\"n2\":" + std::to_string(o.n2);
+  arr("start", o.start.size(), [&](size_t i) { s += std::to_string(o.start[i]); });
+  arr("vb", o.vb.size(), [&](size_t i) { s += std::to_string(o.vb[i]); });
+  arr("mp", o.mp.size(), [&](size_t i) { s += std::to_string(o.mp[i]); });
+  arr("pdim", o.pdim.size(), [&](size_t i) { s += std::to_string(o.pdim[i]); });
+  arr("off", o.off.size(), [&](size_t i) { s += std::to_string(o.off[i]); });
+  arr("sdig", o.sdig.size(), [&](size_t i) { s += std::to_string(o.sdig[i]); });
+  arr("ch", o.ch.size(), [&](size_t i) {
+    const KSBChan& c = o.ch[i];
+    s += "[" + std::to_string(c.kind) + "," + std::to_string(c.tab) + "," + std::to_string(c.dj) + "," +
+         std::to_string(c.si) + "," + std::to_string(c.sj) + "," + std::to_string(c.pfx) + "," + std::to_string(c.qp) +
+         "," + std::to_string(c.xr) + "," + std::to_string(c.dblk) + "," + std::to_string(c.lbit) + "," +
+         std::to_string(c.lwid) + "]";
+  });
+  arr("tab", o.tab.size(), [&](size_t i) { num(o.tab[i]); });
+  arr("dS", o.dS.size(), [&](size_t i) { num(o.dS[i]); });
+  arr("ell_r", o.ell_r.size(), [&](size_t i) { s += std::to_string(o.ell_r[i]); });
+  arr("ell", o.ell_d.size(), [&](size_t i) { num(o.ell_d[i]); });
+  arr("xr", o.xr_flat.size(), [&](size_t i) { s += std::to_string(o.xr_flat[i]); });
+  s += "}";
+  return s;
 }
 
 void free_sector_blk(Plan* p) {

@@ -200,3 +200,60 @@ def emulate_sector(S, x, nvec=1):
             dlt = dlt + Aat(sj, rj + q, nj - qj) - Aat(sj, rj, nj)
         acc[rows] += cf[rows, None] * X[rows + dlt]
     return (acc + dsum[:, None] * X).reshape(-1)
+
+
+def emulate_sector_blk(P, x, nvec=1):
+    """The block-form sector kernel's steps on its exported tables (numpy,
+    one prefix block at a time): prefix digits of the block, its suffix
+    sector t = K - P, block-uniform prefix diagonal and moves, per-suffix
+    diagonal and in-sector moves, coupled channels through the prefix
+    digit's table row and the source-rank tables."""
+    h, K, G, w = P["h"], P["K"], P["G"], P["w"]
+    n0, n1, n2 = P["n0"], P["n1"], P["n2"]
+    start = np.asarray(P["start"], dtype=np.int64)
+    mp, pdim, off = P["mp"], P["pdim"], P["off"]
+    sdig = np.asarray(P["sdig"], dtype=np.int64)
+    tab = np.asarray(P["tab"], dtype=np.float64)
+    dS = np.asarray(P["dS"], dtype=np.float64)
+    ell_r = np.asarray(P["ell_r"], dtype=np.int64).reshape(w, G) if w else np.zeros((0, G), np.int64)
+    ell = np.asarray(P["ell"], dtype=np.float64).reshape(w, G) if w else np.zeros((0, G))
+    xr = np.asarray(P["xr"], dtype=np.int64).reshape(-1, G) if P["xr"] else np.zeros((0, G), np.int64)
+    ch = [dict(zip(("kind", "tab", "dj", "si", "sj", "pfx", "qp", "xr", "dblk", "lbit", "lwid"), c)) for c in P["ch"]]
+    X = np.asarray(x, dtype=np.float64).reshape(-1, nvec)
+    Y = np.zeros_like(X)
+    for b in P["vb"]:
+        dig = [(b // mp[k]) % pdim[k] for k in range(h)]
+        t = K - sum(dig)
+        g = np.arange(off[t], off[t + 1])
+        F = start[b] + np.arange(g.size)
+        pk = sdig[g]
+        digit = lambda c: (pk >> c["lbit"]) & ((1 << c["lwid"]) - 1)
+        d = dS[g].copy()
+        for c in ch[:n0]:
+            d += tab[c["tab"] + dig[c["si"]] * c["dj"] + (dig[c["sj"]] if c["sj"] >= 0 else 0)]
+        rows = {}
+        for i, c in enumerate(ch[n1:], start=n1):
+            npf = dig[c["sj"] if c["pfx"] else c["si"]]
+            rows[i] = (c["tab"] + npf, c["dj"]) if c["pfx"] else (c["tab"] + npf * c["dj"], 1)
+        for i in range(n1, n2):
+            base, mul = rows[i]
+            d += tab[base + mul * digit(ch[i])]
+        acc = d[:, None] * X[F]
+        for c in ch[n0:n1]:
+            cf = tab[c["tab"] + dig[c["si"]] * c["dj"] + dig[c["sj"]]]
+            if cf != 0.0:
+                acc += cf * X[F + (start[b - c["dblk"]] - start[b])]
+        for e in range(w):
+            acc += ell[e, g][:, None] * X[F + ell_r[e, g]]
+        for i in range(n2, len(ch)):
+            c = ch[i]
+            ps = c["sj"] if c["pfx"] else c["si"]
+            if not 0 <= dig[ps] - c["qp"] < pdim[ps]:
+                continue
+            base, mul = rows[i]
+            cf = tab[base + mul * digit(c)]
+            nz = cf != 0.0
+            src = start[b - c["dblk"]] + xr[c["xr"], g[nz]]
+            acc[nz] += cf[nz, None] * X[src]
+        Y[F] = acc
+    return Y.reshape(-1)

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import workloads as W
-from plan_emulator import emulate_sector
+from plan_emulator import emulate_sector, emulate_sector_blk
 
 
 @pytest.fixture(scope="module")
@@ -171,3 +171,59 @@ def test_tavis_cummings_excitation_sectors_with_capped_boson_digits(capi, K):
     x = W.vector(S["Dsec"], 13)
     ref = oracle.sector_apply(sites, terms, K, x)
     assert np.allclose(emulate_sector(S, x), ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+BLK_CASES = [
+    ((2,) * 15, ("spin",) * 15, 7),                                  # one prefix site
+    ((2,) * 16, ("spin",) * 16, 5),                                  # two prefix sites
+    ((6,) + (2,) * 12, ("boson",) + ("spin",) * 12, 6),              # boson prefix
+    ((3, 2) + (2,) * 10 + (5,), ("spin",) * 12 + ("boson",), 7),     # boson in the suffix
+    ((3, 3, 3, 3, 3, 3, 3, 3, 3, 3), ("spin",) * 10, 10),            # spin-1, 3^10 states
+]
+
+
+@pytest.mark.parametrize("dims,kinds,total", BLK_CASES)
+def test_block_form_tables_reproduce_the_projection(capi, dims, kinds, total):
+    """The block form's tables (hm_plan_export bits 2 and 4) run through the
+    numpy emulation of its kernel equal the sector oracle's projection P H
+    P^T x; the suffix sectors partition the suffix tuples, the blocks the
+    retained states."""
+    sites, terms = _conserving(dims, kinds, 12)
+    B = capi.plan_export(sites, terms, 4 | 16 | (total << 8))
+    assert B["ok"]
+    n = oracle.sector_dimension(sites, total)
+    x = W.vector(n, 3)
+    ref = oracle.sector_apply(sites, terms, total, x)
+    got = emulate_sector_blk(B, x)
+    assert np.allclose(got, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+    # structure: suffix sectors cover the suffix tuples, blocks the sector
+    suffix_dims = [d for _, d in sites[B["h"]:]]
+    assert B["off"][-1] == B["G"] == sum(oracle.sector_dimension([("spin", d) for d in suffix_dims], t)
+                                         for t in range(total + 1))
+    sizes = []
+    for b in B["vb"]:
+        P = sum((b // B["mp"][k]) % B["pdim"][k] for k in range(B["h"]))
+        sizes.append(B["off"][total - P + 1] - B["off"][total - P])
+    assert sum(sizes) == n
+    assert [B["start"][b] for b in B["vb"]] == list(np.concatenate([[0], np.cumsum(sizes)[:-1]]))
+    kinds_seen = {c[0] for c in B["ch"]}
+    if B["h"] >= 2:
+        assert kinds_seen >= {0, 1, 2, 3}      # prefix diagonal and moves, coupled diagonal and moves
+
+
+def test_block_form_with_several_right_hand_sides(capi):
+    sites, terms = _conserving((2,) * 15, ("spin",) * 15, 13)
+    B = capi.plan_export(sites, terms, 4 | 16 | (6 << 8))
+    n = oracle.sector_dimension(sites, 6)
+    x = W.vector(n, 4, nvec=3)
+    assert np.allclose(emulate_sector_blk(B, x, 3), oracle.sector_apply(sites, terms, 6, x, nvec=3),
+                       rtol=0, atol=1e-12)
+
+
+def test_block_form_rejections(capi):
+    from paper_2606_02169_gb300._capi import HmError
+    sites = [("spin", 2)] * 16
+    with pytest.raises(HmError):       # empty sector
+        capi.plan_export(sites, [(0, "Sz", -1, "I", 1.0)], 4 | 16 | (17 << 8))
+    with pytest.raises(HmError):       # a lone Sx moves the digit sum
+        capi.plan_export(sites, [(0, "Sx", -1, "I", 1.0)], 4 | 16 | (8 << 8))
