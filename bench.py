@@ -157,11 +157,13 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    # the sources the general apply kernel (plain and prefetching) and the
-    # split pass compile from
-    for f in ("apply.cu", "apply_kernel.cuh", "apply_launch.cuh", "apply_df64.cu", "apply_f32.cu",
+    # the device code of the general apply kernel (its body, arithmetic
+    # policies, launch shapes and the units that instantiate its scalar
+    # variants); a change to how the plan builder derives its tables needs
+    # the records taken again as well
+    for f in ("apply_kernel.cuh", "apply_launch.cuh", "device_common.cuh", "apply_df64.cu", "apply_f32.cu",
               "apply_pf_df64.cu", "apply_pf_f32.cu", "apply_vi_df64.cu", "apply_vi_f32.cu", "apply_pf_vi_df64.cu",
-              "apply_pf_vi_f32.cu", "device_common.cuh", "plan.cpp", "hm_internal.h"):
+              "apply_pf_vi_f32.cu"):
         with open(os.path.join(ROOT, "paper_2606_02169_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -638,6 +640,9 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
     models = W.disorder_ensemble(256, 8, 14, 1000)
     hams = [Hamiltonian(mm.sites, mm.terms) for mm in models]
     nvec = 16
+    if args.tune:   # members that fill the GPU alone take their tuned launch (one tune per chain length)
+        for hh in hams:
+            hh.tune(nvec, torch.float32)
     xs = [W.torch_vector(hh.D * nvec, 1000 + i, dtype=torch.float32, normalize=False) for i, hh in enumerate(hams)]
     ys = [torch.empty_like(t) for t in xs]
     total = sum(hh.D for hh in hams) * nvec

@@ -317,9 +317,11 @@ int hm_krylov_coefficients(const double* alpha, const double* beta, int32_t m, d
 
 /* Batched apply over many plans of uneven size: one persistent launch per
  * 128 instances walks an (instance, block[, chunk]) work list; an instance
- * with enough work to fill the GPU by itself gets a plain launch of the
- * general kernel instead. Every member's y equals hm_apply_ex with the
- * general kernel (flag bit 4) on it, bit for bit. hs[n] stay owned by the caller
+ * with enough work to fill the GPU by itself gets the launch hm_apply would
+ * make for it instead (its hm_tune choice, else the general kernel's
+ * default). A queued member's y, and an untuned member's y, equals
+ * hm_apply_ex with the general kernel (flag bit 4) on it, bit for bit; a
+ * tuned member that fills the GPU gets hm_apply's y. hs[n] stay owned by the caller
  * and must outlive the batch; each call reads the members' tables as they
  * are then (a CUDA graph captured before an hm_set_coefficients on a member
  * must be captured again). xs[b], ys[b]: device pointers (arrays of n

@@ -458,14 +458,9 @@ int launch_batch(Plan* b, const void* const* xs, void* const* ys, long long nvec
   for (size_t i = 0; i < b->members.size(); ++i) {
     Plan* p = b->members[i];
     if (fills_gpu(p, nvec)) {
-      // the general kernel, whose block code the persistent queue shares:
-      // every member's y is that kernel's, bit for bit
-      TuneCfg c = tuned_cfg(p, dt, nvec);
-      if (c.kern != 1) c = TuneCfg{};
-      c.kern = 1;
-      c.split = 0;  // one pass and the queued members' group arithmetic
-      c.vinv = 0;
-      int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, c, false);
+      // the launch hm_apply makes for this member: its tuned choice, or the
+      // general kernel's default (the block code the persistent queue shares)
+      int rc = apply_on(p, false, xs[i], ys[i], nvec, dt, s, tuned_cfg(p, dt, nvec), false);
       if (rc) return rc;
       continue;
     }

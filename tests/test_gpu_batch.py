@@ -77,3 +77,22 @@ def test_batch_mixing_large_and_small_instances(dtype):
     ref = oracle.apply(models[0].sites, models[0].terms, xn, nvec=nvec)
     scale = np.full(xn.size, row_scale_bound(models[0], np.abs(xn).max()))
     check_close(ys[0].double().cpu().numpy(), ref, scale, TOL_F32 if dtype == "f32" else TOL_F64, "large")
+
+
+def test_tuned_large_member_takes_its_tuned_launch():
+    """A member that fills the GPU alone runs the launch hm_apply makes for
+    it; after hm_tune that is the tuned choice (here possibly a split or
+    vector-lane variant), and the queued members still equal the general
+    kernel bit for bit."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Batch
+    models = [W.xxz_spin1_chain(13, seed=81)] + W.disorder_ensemble(count=4, nmin=3, nmax=6, base_seed=82)
+    hams = [ham(m) for m in models]
+    nvec = 16
+    hams[0].tune(nvec, torch.float32)
+    xs = [torch.from_numpy(W.vector(h.D, 400 + i, nvec=nvec)).to("cuda", torch.float32) for i, h in enumerate(hams)]
+    ys = Batch(hams).apply(xs)
+    torch.cuda.synchronize()
+    assert torch.equal(hams[0].apply(xs[0]), ys[0])
+    for i in range(1, len(hams)):
+        assert torch.equal(hams[i].apply_ex(xs[i], kernel="general"), ys[i]), i
