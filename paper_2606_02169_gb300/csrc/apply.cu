@@ -65,7 +65,20 @@ __global__ void __launch_bounds__(256) k_split_f64(const double* __restrict__ x,
   const double2* __restrict__ x2 = reinterpret_cast<const double2*>(x);
   float4* __restrict__ xs4 = reinterpret_cast<float4*>(xs);
   bool bad = false;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+  const long long st = (long long)gridDim.x * blockDim.x;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i + 3 * st < n2; i += 4 * st) {  // four 16-byte loads in flight per thread
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = __ldcs(x2 + i + u * st);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 a = split_f64(v[u].x), b = split_f64(v[u].y);
+      bad |= outside_df_window(v[u].x, wlo, whi) | outside_df_window(v[u].y, wlo, whi);
+      xs4[i + u * st] = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+  for (; i < n2; i += st) {
     const double2 v = __ldcs(x2 + i);
     const float2 a = split_f64(v.x), b = split_f64(v.y);
     bad |= outside_df_window(v.x, wlo, whi) | outside_df_window(v.y, wlo, whi);
