@@ -1,7 +1,8 @@
 """hm_apply on vectors in pinned host memory: the kernels read x and write y
 over the CPU-GPU link (FP64: the split pass reads x once; FP32: x is first
 copied once into device scratch). Results equal the same call on device
-vectors bit for bit; pageable host memory is rejected."""
+vectors bit for bit, on one stream and with calls alternating between two
+streams; pageable host memory is rejected."""
 import numpy as np
 import pytest
 
@@ -50,3 +51,17 @@ def test_pageable_host_vectors_are_rejected():
     assert rc == C.HM_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         h.apply(torch.from_numpy(xp))
+
+
+def test_host_vector_calls_on_two_streams():
+    torch = torch_cuda()
+    m = W.random_model([2, 3, 2, 3, 2, 3, 2, 3, 2, 3], None, nterms=30, seed=6)
+    h = ham(m)
+    xs = [torch.from_numpy(W.vector(h.D, 20 + i)) .pin_memory() for i in range(4)]
+    ys = [torch.empty(h.D, dtype=torch.float64, pin_memory=True) for _ in range(4)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i in range(4):
+        h.apply(xs[i], out=ys[i], stream=streams[i % 2])
+    torch.cuda.synchronize()
+    for i in range(4):
+        assert torch.equal(ys[i], h.apply(xs[i].cuda()).cpu()), i
