@@ -170,11 +170,16 @@ int32_t hm_num_terms(hm_handle h);
  * and one coefficient per state); results are bit-identical to one
  * right-hand side per lane.
  * Kernel: the general kernel (block-uniform hops as coalesced gathers, hops
- * inside the low block from a per-plan table) unless hm_tune chose another:
- * the general kernel on a small low block, or the staged kernel (each hop's
- * source range streamed into shared memory by bulk asynchronous copies;
- * its bounded waits report to hm_device_status). Those two build extra
- * tables on their first call for each nvec, which hm_tune makes. */
+ * inside the low block from a per-plan table) unless hm_tune chose another
+ * launch: a variant of the general kernel (elements per thread, register
+ * cap, prefetching, one group factor per lane, the top-site split into two
+ * passes, one right-hand side per lane), the general kernel on a small low
+ * block, the leaf-tiled kernel, or the staged kernel (each hop's source
+ * range streamed into shared memory by bulk asynchronous copies; its
+ * bounded waits report to hm_device_status). The small-block, split, tile
+ * and staged forms build extra tables on their first call for each nvec
+ * (or split size), which hm_tune makes; a first call inside a stream capture
+ * runs the general kernel's default instead. */
 int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* Diagnostic variant of hm_apply (it ignores hm_tune's choice). flags
