@@ -16,9 +16,18 @@ from .hamiltonian import Hamiltonian
 
 
 def _sync_coefs(ham: Hamiltonian, coefs: torch.Tensor):
+    """Bring the plan's coefficients up to date with `coefs`. The plan's
+    tables are rebuilt on the host, so a changed coefficient tensor costs one
+    device-to-host read; an unchanged one (the same tensor, not modified in
+    place since the last call: same version counter) costs nothing and does
+    not synchronise the host."""
+    ref = getattr(ham, "_coef_ref", None)
+    if ref is not None and ref[0] is coefs and ref[1] == coefs._version:
+        return
     c = coefs.detach().double().cpu().tolist()
     if c != ham.coefs:
         ham.set_coefficients(c)
+    ham._coef_ref = (coefs, coefs._version)   # holds the tensor: its identity stays unique
 
 
 class HamApply(torch.autograd.Function):

@@ -77,8 +77,7 @@ static cudaError_t launch_nv(const KPlan& k, const void* x, void* y, long long n
 }
 
 // 16-byte elements (4 FP32 or 2 double-float right-hand sides per lane):
-// at most 4 of them per thread and no register-capped variant (both would
-// spill their accumulators).
+// at most 4 of them per thread (more would spill their accumulators).
 template <int AR>
 constexpr bool wide_elem() {
   return sizeof(typename Ar<AR>::TX) == 16;
@@ -88,7 +87,7 @@ template <int AR, int S, int PF, bool VI>
 static cudaError_t launch_shape(const KPlan& k, const void* x, void* y, long long nvec, int nchunks,
                                 cudaStream_t st, TuneCfg cfg) {
   const KGate g{cfg.gate, cfg.gate_run};
-  if constexpr (AR != AR_F64 && !wide_elem<AR>()) {
+  if constexpr (AR != AR_F64) {
     if (cfg.mb) {
       if (nvec == 1) return launch_nv<AR, S, true, 1, PF, VI>(k, x, y, nvec, nchunks, st, cfg.ctas, g);
       return launch_nv<AR, S, false, 1, PF, VI>(k, x, y, nvec, nchunks, st, cfg.ctas, g);

@@ -102,6 +102,7 @@ class Hamiltonian:
         arr = (ctypes.c_double * max(1, self.nterms))(*c)
         C.check(self._lib.hm_set_coefficients(self._h, arr), "hm_set_coefficients")
         self.coefs = c
+        self._coef_ref = None   # the autograd wrappers compare against this
 
     # -- y = H x -------------------------------------------------------------
     def _nvec(self, x):

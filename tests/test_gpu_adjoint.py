@@ -150,3 +150,28 @@ def test_residual_loss_gradients_vs_oracle_4x5():
     gh = gt[3 * nb:]
     for got, ref in ((J.grad, gJ), (Dl.grad, gD), (hf.grad, gh)):
         assert np.allclose(got.numpy(), ref, rtol=1e-9, atol=1e-10)
+
+
+def test_autograd_coefficient_sync_only_when_changed():
+    """The autograd wrapper re-plans only when the coefficient tensor is a
+    different tensor or was modified in place; an unchanged tensor skips the
+    host read. A direct set_coefficients between calls is honoured."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300.autograd import hamiltonian_apply
+    m = W.heisenberg_ring(8)
+    h = ham(m)
+    x = torch.from_numpy(W.vector(h.D, 3)).cuda()
+    coefs = torch.tensor([t[4] for t in m.terms], dtype=torch.float64, device="cuda")
+    reads = []
+    orig = h.set_coefficients
+    h.set_coefficients = lambda c: (reads.append(1), orig(c))[1]
+    y0 = hamiltonian_apply(h, coefs, x)
+    y1 = hamiltonian_apply(h, coefs, x)           # same tensor, unchanged: no re-plan
+    assert torch.equal(y0, y1) and len(reads) == 0
+    with torch.no_grad():
+        coefs.mul_(2.0)                           # in place: version bump, re-plan
+    y2 = hamiltonian_apply(h, coefs, x)
+    assert len(reads) == 1 and torch.allclose(y2, 2 * y0, rtol=1e-13, atol=0)
+    orig([t[4] for t in m.terms])                 # direct update back to the original
+    y3 = hamiltonian_apply(h, coefs, x)           # must re-sync to 2x
+    assert len(reads) == 2 and torch.allclose(y3, 2 * y0, rtol=1e-13, atol=0)
