@@ -797,11 +797,17 @@ def variants(args, h, m, x, y, ms_f64, stream, hbm):
         yd = torch.empty_like(xd)
         k = 10
         res[name] = timed(lambda: hd.apply(xd, out=yd), k, 3, 1, stream) / k
+        if name == "complex_h":
+            # the one-pass complex kernel and the two real passes (one
+            # column per lane) with their combine, each as an explicit choice
+            res["one_pass"] = timed(lambda: hd.apply_ex(xd, out=yd), k, 3, 1, stream) / k
+            res["two_pass"] = timed(lambda: hd.apply_ex(xd, out=yd, scalar=True), k, 3, 1, stream) / k
         del hd, xd, yd
         torch.cuda.empty_cache()
     out["complex_h_dm_chain_n26_c128"] = {
         "D": 2 ** nd, "ms_complex_h": res["complex_h"], "gstates_s_complex_h": 2 ** nd / res["complex_h"] / 1e6,
         "hbm_frac_algorithmic": 32 * 2 ** nd / res["complex_h"] / 1e6 / hbm,
+        "ms_one_pass_kernel": res["one_pass"], "ms_two_passes_and_combine": res["two_pass"],
         "ms_real_h_complex_x": res["real_h"], "complex_h_over_real_h": res["complex_h"] / res["real_h"]}
     return out
 

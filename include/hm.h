@@ -25,13 +25,20 @@
  * hm_batch_apply, hm_tune, hm_tuned_config and hm_lanczos accept complex
  * dtypes, hm_evolve requires one. A term list with imaginary matrix
  * elements (Sy factors: a lone Sy, Sx Sy, ...) gives a complex H = H_re +
- * i H_im, held as two real operators on the same kernels: y = H_re x +
- * i H_im x costs two real applies of the 2*nvec columns and one combining
- * pass. Such plans need complex storage (real dtypes give
- * HM_ERR_COMPLEX_REQUIRED) and support hm_apply, hm_apply_adjoint (gx =
- * H^dagger gy only), hm_lanczos, hm_evolve, hm_tune, hm_set_coefficients;
- * hm_apply_ex, coupling gradients, batches and sectors return
- * HM_ERR_UNSUPPORTED.
+ * i H_im, held as two real operators on the same sites: y = H_re x +
+ * i H_im x runs as two real applies of the 2*nvec columns and one
+ * combining pass, or, where hm_tune measured it faster, as one pass in
+ * which a thread forms both operators' sums for each (re, im) element and
+ * combines them in registers (one read of the state's digits, one write of
+ * y; it needs x and y aligned to one complex element, 8 or 16 bytes,
+ * HM_C64 x in device memory and both operators' block lists within shared
+ * memory, else the two passes run). With the general kernel in both real
+ * passes the two forms give the same bits. Such
+ * plans need complex storage (real dtypes give HM_ERR_COMPLEX_REQUIRED)
+ * and support hm_apply, hm_apply_ex (flag bits 0, 1, 4 and 13, see
+ * there), hm_apply_adjoint (gx = H^dagger gy only), hm_lanczos, hm_evolve,
+ * hm_tune, hm_set_coefficients; coupling gradients, batches and sectors
+ * return HM_ERR_UNSUPPORTED.
  * Every call is asynchronous on the given CUDA stream (NULL = legacy default
  * stream) unless stated otherwise. Plans are library-owned. Applies of one
  * plan (hm_apply, hm_batch_apply) may run on several streams at once: the
@@ -219,6 +226,13 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, 
  * v * sum(u x) per element (fewer registers and operations; rounds
  * differently, within the same tolerance); ignored elsewhere. ctas > 0
  * forces the persistent grid size (0 = library default).
+ * A complex H (complex storage only) takes bits 0, 1 (H^dagger = H_re^T -
+ * i H_im^T), 2, 4 (no effect) and 13; other bits give HM_ERR_UNSUPPORTED.
+ * Without bit 13 the one-pass complex kernel runs, with bit 2 its
+ * register-capped variant (three resident CTAs per SM) (HM_ERR_UNSUPPORTED
+ * where it is not available, see Vectors above); with bit 13, two real
+ * applies of the general kernel's default launch and the combining pass.
+ * All three give the same bits.
  * Same ownership and error rules as hm_apply. */
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream);
@@ -345,7 +359,10 @@ int hm_batch_apply(hm_handle batch, const void* const* xs, void* const* ys, int6
  * site dimensions and channel counts, for hm_apply, hm_apply_adjoint (gx) and
  * hm_lanczos. Synchronous. The variants of one kernel compute the same y bit
  * for bit; the kernels sum in different orders (all within the FP64 /
- * FP32 tolerances). */
+ * FP32 tolerances). For a complex H (complex dtype) it tunes both real
+ * operators on the 2*nvec columns, then times the two tuned real passes
+ * with their combine against the one-pass complex kernel and its
+ * register-capped variant and keeps the fastest for that (nvec, dtype). */
 int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
 
 /* The launch choice hm_tune stored for (nvec, dtype): out[0] = grid size,
@@ -353,7 +370,10 @@ int hm_tune(hm_handle h, int64_t nvec, hm_dtype dtype, void* stream);
  * out[2] = bit 0 register-cap variant, bit 1 small low block, bit 2
  * prefetching, bit 3 one right-hand side per lane, bit 4 top-site split,
  * bit 5 one group factor per lane, bits 8..11 the split's number of
- * leading sites (general kernel),
+ * leading sites (general kernel), bit 6 (complex H asked with a complex
+ * dtype) the one-pass complex kernel instead of two tuned real passes,
+ * bit 7 its register-capped variant; the other fields describe H_re's
+ * tuned launch,
  * out[3] = kernel (1 general, 2 tile, 3 staged) (int32_t[4], host; 0 each =
  * library default). No counterpart in the paper (a diagnostic). */
 int hm_tuned_config(hm_handle h, int64_t nvec, hm_dtype dtype, int32_t* out);

@@ -22,7 +22,7 @@ SOURCES = ["capi.cpp", "plan.cpp", "tile_plan.cpp", "apply.cu", "apply_f32.cu", 
            "stream_f32.cu", "stream_df64.cu", "stream_f64.cu", "apply_pf_f32.cu", "apply_pf_df64.cu",
            "apply_pf_f64.cu", "apply_v2_f32.cu", "apply_v4_f32.cu", "apply_v_df64.cu",
            "apply_batch_f32.cu", "apply_batch_df64.cu", "apply_vi_df64.cu", "apply_vi_f32.cu",
-           "apply_pf_vi_df64.cu", "apply_pf_vi_f32.cu"]
+           "apply_pf_vi_df64.cu", "apply_pf_vi_f32.cu", "apply_cx_f32.cu", "apply_cx_df64.cu", "apply_cx_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,6 +12,10 @@
 
 namespace hm {
 
+template <int AR>
+cudaError_t launch_apply_cx_t(const KPlan& kr, const KPlan& ki, const void* x, void* y, long long nvec,
+                              cudaStream_t st, int ctas, KGate gate, bool conj, bool cap);
+
 template <int AR, bool VI>
 cudaError_t launch_apply_t(const KPlan& k, const void* x, void* y, long long nvec, cudaStream_t st, TuneCfg cfg);
 template <int AR>
@@ -404,17 +408,81 @@ __global__ void k_cmix(T* __restrict__ y, const T* __restrict__ t, T sg, long lo
   }
 }
 
-// Complex H = H_re + i H_im: two real applies on the 2 * nvec (re, im)
-// columns, then one combining pass. The adjoint H^dagger = H_re^T - i H_im^T.
-int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s) {
+// One pass over both real operators (apply_cx.cuh): FP32 storage on float
+// (re, im) pairs; FP64 storage in double-float on the split x, with the
+// native FP64 pass gated on the split's range flag (as in apply_on), or
+// native FP64 throughout. 1: the call does not allow it (vectors not aligned
+// to one complex element, FP32 x in host memory, lists beyond shared memory).
+static int apply_complex_fused(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt,
+                               cudaStream_t s, bool native, int ctas, bool cap) {
+  const KPlan& kr = adjoint ? p->kt : p->k;
+  const KPlan& ki = adjoint ? p->im->kt : p->im->k;
+  const uintptr_t el = dt == HM_F32 ? 8 : 16;
+  if (!aligned(x, el) || !aligned(y, el) || (dt == HM_F32 && host_resident(x))) return 1;
+  if (!cx_compatible(kr, ki) || cx_lists_bytes<AR_DF64V2>(kr) + cx_lists_bytes<AR_DF64V2>(ki) > 227 * 1024) return 1;
+  cudaError_t e;
+  if (dt == HM_F32) {
+    e = launch_apply_cx_t<AR_F32V2>(kr, ki, x, y, nvec, s, ctas, KGate{nullptr, 0}, adjoint, cap);
+  } else if (native || !p->df_ok || !p->im->df_ok) {
+    e = launch_apply_cx_t<AR_F64V2>(kr, ki, x, y, nvec, s, ctas, KGate{nullptr, 0}, adjoint, cap);
+  } else {
+    Scratch xsb;
+    const float2* xs = nullptr;
+    const int* range = nullptr;
+    int rc = split_vector(x, vec_states(p) * nvec * 2, s, xsb, &xs, &range, std::max(p->df_xlo, p->im->df_xlo),
+                          std::min(p->df_xhi, p->im->df_xhi));
+    if (rc) return rc;
+    e = launch_apply_cx_t<AR_DF64V2>(kr, ki, xs, y, nvec, s, ctas, KGate{range, 0}, adjoint, cap);
+    if (e == cudaSuccess)  // native FP64 pass, runs only when the split flagged x
+      e = launch_apply_cx_t<AR_F64V2>(kr, ki, x, y, nvec, s, ctas, KGate{range, 1}, adjoint, cap);
+    if (e == cudaErrorInvalidConfiguration) return cuda_fail(e, "complex apply launch");
+  }
+  if (e == cudaErrorInvalidConfiguration) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "complex apply launch");
+  return HM_OK;
+}
+
+// Complex H = H_re + i H_im. The adjoint H^dagger = H_re^T - i H_im^T. The
+// two-pass form: two real applies on the 2 * nvec (re, im) columns, then
+// one combining pass. Untuned plans take the two-pass form: measured on the
+// Dzyaloshinskii-Moriya ring (N = 26) it is as fast as the one-pass kernel
+// for complex128 and faster for complex64.
+constexpr int kCxDefaultForm = 2;
+
+int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+                  int mode, bool native, int ctas, bool cap) {
   const long long nc = 2 * nvec;
-  int rc = apply_on(p, adjoint, x, y, nc, dt, s, tuned_cfg(p, dt, nc), false);
+  int form = 2;
+  if (mode == 0) {
+    const auto it = p->cx_form.find({(int)dt, nvec});
+    form = it == p->cx_form.end() ? kCxDefaultForm : it->second;
+  } else if (mode == 2) {
+    form = cap ? 1 : 0;
+  }
+  if (form != 2) {
+    const int rc = apply_complex_fused(p, adjoint, x, y, nvec, dt, s, native, ctas, form == 1);
+    if (rc != 1) return rc;
+    if (mode == 2) {
+      set_error("the one-pass complex kernel needs x and y aligned to one complex element, FP32 x in device "
+                "memory, and both operators' block lists within shared memory");
+      return HM_ERR_UNSUPPORTED;
+    }
+  }
+  TuneCfg c0 = tuned_cfg(p, dt, nc), c1 = tuned_cfg(p->im, dt, nc);
+  if (mode == 1) {  // an explicit two-pass request: the general kernel's default launch
+    c0 = c1 = TuneCfg{};
+    c0.ctas = c1.ctas = ctas;
+  }
+  int rc = apply_on(p, adjoint, x, y, nc, dt, s, c0, native);
   if (rc) return rc;
   Scratch tb;
   const long long n = vec_states(p) * nc;
   rc = scratch_alloc(tb, (size_t)n * (dt == HM_F32 ? 4 : 8), s);
   if (rc) return rc;
-  rc = apply_on(p->im, adjoint, x, tb.ptr, nc, dt, s, tuned_cfg(p->im, dt, nc), false);
+  rc = apply_on(p->im, adjoint, x, tb.ptr, nc, dt, s, c1, native);
   if (rc) return rc;
   const long long np = n / 2;
   const int grid = (int)std::max<long long>(1, std::min<long long>((np + 255) / 256, (long long)num_sms() * 8));

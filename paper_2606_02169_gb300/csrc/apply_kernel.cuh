@@ -127,6 +127,19 @@ __host__ __device__ inline size_t lists_bytes(int n_hh, int n_mem, int n_grp, in
          al(n_hh * sizeof(KChan)) + al(n_mem * sizeof(KMember)) + al(n_grp * sizeof(KGroup));
 }
 
+// shared memory of one plan's lists in the complex kernel (16-byte aligned
+// so that the second plan's lists follow)
+template <int AR>
+__host__ __device__ inline size_t cx_lists_bytes(const KPlan& k) {
+  return (lists_bytes<AR>(k.n_hh_diag + k.n_hh, k.n_mem, k.n_grp_diag + k.n_grp, k.n_grp_diag) + 15) & ~size_t(15);
+}
+
+// two plans on the same sites (the real and imaginary parts of a complex H)
+// share their low block, packed low digits and high/low split
+inline bool cx_compatible(const KPlan& a, const KPlan& b) {
+  return a.B == b.B && a.nblk == b.nblk && a.nhigh == b.nhigh && a.D == b.D;
+}
+
 template <int AR>
 __device__ inline Lists<AR> carve(unsigned char* sm, int n_hh, int n_mem, int n_grp, int n_grpd) {
   using C = typename Ar<AR>::C;
@@ -296,20 +309,36 @@ struct NvDiv {
   }
 };
 
-// One chunk of NT*S elements starting at element `e_start` of low block blk
-// (uniforms already in L). FULL: every element of the chunk lies inside the
-// block, so no per-element bounds predicates are needed. NV1: nvec == 1.
-// VINV: the low digit of every factorised group is the same for the
-// thread's S elements (its period M_k d_k divides their stride), so each
-// group has one v per thread and member coefficients v u are formed once.
+// The thread's elements e0 + s NT of a chunk of low block blk: whether each
+// lies inside the block, its state within the block and that state's packed
+// low digits (the same for every plan on these sites).
+template <int S, bool FULL, bool NV1>
+__device__ __forceinline__ void chunk_states(const KPlan& P, int belems, int e0, NvDiv nvdiv, bool (&ok)[S],
+                                             int (&lo)[S], uint32_t (&pk)[S]) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = e0 + s * kNT;
+    ok[s] = FULL || e < belems;
+    lo[s] = ok[s] ? (NV1 ? e : nvdiv(e)) : 0;
+    pk[s] = __ldg(P.ptab + lo[s]);
+  }
+}
+
+// acc[s] = (H x) of the thread's element s of a chunk (uniforms of the block
+// already in L; xb = x + the element's index for s = 0). FULL: every element
+// of the chunk lies inside the block, so no per-element bounds predicates
+// are needed. NV1: nvec == 1. VINV: the low digit of every factorised group
+// is the same for the thread's S elements (its period M_k d_k divides their
+// stride), so each group has one v per thread and member coefficients v u
+// are formed once.
 template <int AR, int S, bool FULL, bool NV1, int PF = 0, bool VINV = false>
-__device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
-                                            const typename Ar<AR>::TX* __restrict__ x,
-                                            typename Ar<AR>::TY* __restrict__ y, int nvec_rt, NvDiv nvdiv,
-                                            long long blk, int e_start, typename Ar<AR>::TX* pfbuf = nullptr) {
+__device__ __forceinline__ void chunk_sum(const KPlan& P, const Lists<AR>& L,
+                                          const typename Ar<AR>::TX* __restrict__ x, int nvec_rt, int e0,
+                                          const typename Ar<AR>::TX* __restrict__ xb, const bool (&ok)[S],
+                                          const int (&lo)[S], const uint32_t (&pk)[S],
+                                          typename Ar<AR>::Acc (&acc)[S], typename Ar<AR>::TX* pfbuf) {
   using A = Ar<AR>;
   using TX = typename A::TX;
-  using TY = typename A::TY;
   using C = typename A::C;
   using Acc = typename A::Acc;
   using Dsum = typename A::Dsum;
@@ -317,23 +346,6 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
   constexpr int NT = kNT;
   const int nvec = NV1 ? 1 : nvec_rt;
   const C* __restrict__ tab = A::tab(P);
-  const int belems = P.B * nvec;
-  const long long ebase = blk * (long long)belems;
-  const int e0 = e_start + (int)threadIdx.x;
-  const TX* __restrict__ xb = x + ebase + e0;  // own element s at xb[s*NT]
-
-  bool ok[S];
-  int lo[S];
-  uint32_t pk[S];
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = e0 + s * NT;
-    ok[s] = FULL || e < belems;
-    lo[s] = ok[s] ? (NV1 ? e : nvdiv(e)) : 0;
-    pk[s] = __ldg(P.ptab + lo[s]);
-  }
-
-  Acc acc[S];
   // ---- diagonal (Sec. IV.A diag rule, Sec. IV.B zz collapse, App. B/C) ----
   {
     const C* __restrict__ dtab = A::diag(P);
@@ -454,6 +466,28 @@ __device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
       }
     }
   }
+}
+
+// One chunk of NT*S elements starting at element `e_start` of low block blk
+// (uniforms already in L): the sums of chunk_sum, stored.
+template <int AR, int S, bool FULL, bool NV1, int PF = 0, bool VINV = false>
+__device__ __forceinline__ void apply_chunk(const KPlan& P, const Lists<AR>& L,
+                                            const typename Ar<AR>::TX* __restrict__ x,
+                                            typename Ar<AR>::TY* __restrict__ y, int nvec_rt, NvDiv nvdiv,
+                                            long long blk, int e_start, typename Ar<AR>::TX* pfbuf = nullptr) {
+  using A = Ar<AR>;
+  using TY = typename A::TY;
+  constexpr int NT = kNT;
+  const int nvec = NV1 ? 1 : nvec_rt;
+  const int belems = P.B * nvec;
+  const long long ebase = blk * (long long)belems;
+  const int e0 = e_start + (int)threadIdx.x;
+  bool ok[S];
+  int lo[S];
+  uint32_t pk[S];
+  chunk_states<S, FULL, NV1>(P, belems, e0, nvdiv, ok, lo, pk);
+  typename A::Acc acc[S];
+  chunk_sum<AR, S, FULL, NV1, PF, VINV>(P, L, x, nvec, e0, x + ebase + e0, ok, lo, pk, acc, pfbuf);
   // ---- store: one write per output element (the second pass of a
   //      top-site split adds its rounded sum to the first pass's value) ----
   TY* __restrict__ yb = y + ebase + e0;

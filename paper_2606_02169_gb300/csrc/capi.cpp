@@ -123,14 +123,6 @@ static int build_companion(Plan* p) {
   return build_plan(p->im);
 }
 
-static int complex_only(const Plan* p, const char* what) {
-  if (p && p->im) {
-    set_error(std::string(what) + " is not available for a complex H (imaginary matrix elements)");
-    return HM_ERR_UNSUPPORTED;
-  }
-  return HM_OK;
-}
-
 static int needs_complex_storage() {
   set_error("the term list has imaginary matrix elements (e.g. a lone Sy): use HM_C128 or HM_C64 storage");
   return HM_ERR_COMPLEX_REQUIRED;
@@ -248,10 +240,24 @@ int hm_apply(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype dtyp
 int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype dtype, int32_t flags,
                 int32_t ctas, void* stream) {
   Plan* p = as_plan(h);
+  const bool cx = dtype == HM_C128 || dtype == HM_C64;
   long long nvec = nvec_in;
   real_view(dtype, nvec);
   int rc = check_vec_args(p, x, y, nvec, dtype);
   if (rc) return rc;
+  if (p->im) {  // complex H: bits 0 (native FP64), 1 (H^dagger), 2 (register cap), 4 (no effect), 13 (two passes)
+    if (flags & ~(1 | 2 | 4 | 16 | 8192)) {
+      set_error("hm_apply_ex on a complex H takes flag bits 0, 1, 2, 4 and 13 only");
+      return HM_ERR_UNSUPPORTED;
+    }
+    if ((flags & 4) && (flags & 8192)) {
+      set_error("flag bit 2 (the register-capped one-pass kernel) does not combine with bit 13 (two passes)");
+      return HM_ERR_INVALID_ARG;
+    }
+    if (!cx) return needs_complex_storage();
+    return apply_complex(p, (flags & 2) != 0, x, y, nvec / 2, dtype, (cudaStream_t)stream, (flags & 8192) ? 1 : 2,
+                         (flags & 1) != 0, ctas > 0 ? ctas : 0, (flags & 4) != 0);
+  }
   if (p->sector) {  // sector plans: bit 4 selects the per-row kernel, nothing else applies
     if (flags & ~16) {
       set_error("hm_apply_ex on a sector plan takes flag bit 4 (the per-row kernel) only");
@@ -259,7 +265,6 @@ int hm_apply_ex(hm_handle h, const void* x, void* y, int64_t nvec_in, hm_dtype d
     }
     return launch_sector(p, x, y, nvec, dtype, (cudaStream_t)stream, (flags & 16) != 0);
   }
-  if ((rc = complex_only(p, "hm_apply_ex"))) return rc;
   TuneCfg cfg;
   cfg.ctas = ctas > 0 ? ctas : 0;
   cfg.mb = (flags >> 2) & 1;
@@ -467,6 +472,7 @@ int hm_destroy(hm_handle h) {
 // dimensions and channel counts. Each candidate: one untimed launch, then the
 // minimum of three event-timed launches.
 static int tune_plan(Plan* p, long long nvec, hm_dtype dtype, void* stream);
+static int tune_complex(Plan* p, long long ncx, hm_dtype dtype, void* stream);
 
 int hm_tune(hm_handle h, int64_t nvec_in, hm_dtype dtype, void* stream) {
   Plan* p = as_plan(h);
@@ -478,8 +484,61 @@ int hm_tune(hm_handle h, int64_t nvec_in, hm_dtype dtype, void* stream) {
   }
   if (int rc = no_sector(p, "hm_tune")) return rc;
   int rc = tune_plan(p, nvec, dtype, stream);
-  // complex H: both real parts are applied to the 2 * nvec columns
+  // complex H: both real parts are applied to the 2 * nvec columns; then
+  // the one-pass complex kernel against the two tuned passes
   if (rc == HM_OK && p->im) rc = tune_plan(p->im, nvec, dtype, stream);
+  if (rc == HM_OK && p->im && nvec % 2 == 0) rc = tune_complex(p, nvec / 2, dtype, stream);
+  return rc;
+}
+
+// Complex H on ncx complex right-hand sides: time the two separately tuned
+// real passes with their combine, the one-pass kernel and its
+// register-capped variant (one untimed call, then the minimum of three),
+// and keep the fastest for apply_complex.
+static int tune_complex(Plan* p, long long ncx, hm_dtype dtype, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->D * 2 * ncx * esize(dtype);
+  void *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "tune scratch x");
+  e = cudaMalloc(&y, bytes);
+  if (e != cudaSuccess) { cudaFree(x); return cuda_fail(e, "tune scratch y"); }
+  cudaMemsetAsync(x, 0, bytes, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = HM_OK;
+  auto time_mode = [&](int mode, bool cap) {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4 && rc == HM_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = apply_complex(p, false, x, y, ncx, dtype, s, mode, false, 0, cap);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = HM_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    return tmin;
+  };
+  int form = 2;
+  float tbest = time_mode(3, false);
+  for (int f = 0; f < 2 && rc == HM_OK; ++f) {
+    const float t = time_mode(2, f == 1);
+    if (rc == HM_ERR_UNSUPPORTED) {  // the one-pass kernel does not fit this plan or these vectors
+      rc = HM_OK;
+      break;
+    }
+    if (t < tbest) {
+      tbest = t;
+      form = f;
+    }
+  }
+  if (rc == HM_OK) p->cx_form[{(int)dtype, ncx}] = form;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
   return rc;
 }
 
@@ -663,6 +722,7 @@ int hm_device_status(int32_t* status, int32_t clear) {
 /* Launch choice hm_tune stored for (nvec, dtype); see include/hm.h. */
 int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) {
   Plan* p = as_plan(h);
+  const bool cx = dtype == HM_C128 || dtype == HM_C64;
   long long nvec = nvec_in;
   real_view(dtype, nvec);
   if (!p || p->is_batch || !out) {
@@ -674,6 +734,12 @@ int hm_tuned_config(hm_handle h, int64_t nvec_in, hm_dtype dtype, int32_t* out) 
   out[1] = c.s;
   out[2] = c.mb | (c.small << 1) | (c.pf << 2) | (c.scalar << 3) | (c.split << 4) | (c.vinv << 5) |
            (c.split_T << 8);
+  if (cx && p->im) {  // complex H: the choice between one pass and two tuned passes
+    const auto it = p->cx_form.find({(int)dtype, nvec / 2});
+    const int form = it == p->cx_form.end() ? -1 : it->second;
+    if (form == 0 || form == 1) out[2] |= 1 << 6;
+    if (form == 1) out[2] |= 1 << 7;
+  }
   out[3] = c.kern;
   return HM_OK;
 }

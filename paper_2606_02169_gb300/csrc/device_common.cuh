@@ -26,7 +26,7 @@
 
 namespace hm {
 
-enum { AR_F32 = 0, AR_DF64 = 1, AR_F64 = 2, AR_F32V2 = 3, AR_F32V4 = 4, AR_DF64V2 = 5 };
+enum { AR_F32 = 0, AR_DF64 = 1, AR_F64 = 2, AR_F32V2 = 3, AR_F32V4 = 4, AR_DF64V2 = 5, AR_F64V2 = 6 };
 
 // Launch gate: a kernel runs iff flag == NULL or (*flag != 0) == run. A
 // double-float apply (run = 0) and its native FP64 fallback (run = 1) are
@@ -303,6 +303,35 @@ template <> struct Ar<AR_DF64V2> : Ar<AR_DF64> {
   __device__ static TY out(Acc a) { return make_double2(df_to_double(a.a), df_to_double(a.b)); }
   __device__ static TY add_out(TY a, TY b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
 };
+
+template <> struct Ar<AR_F64V2> : Ar<AR_F64> {
+  using TX = double2;  // two consecutive right-hand sides (or the (re, im) of one complex value)
+  using TY = double2;
+  using Acc = double2;
+  __device__ static Acc azero() { return make_double2(0.0, 0.0); }
+  __device__ static void fma(Acc& a, C c, TX x) {
+    a.x = __fma_rn(c, x.x, a.x);
+    a.y = __fma_rn(c, x.y, a.y);
+  }
+  __device__ static Acc dmul(Dsum d, TX x) { return make_double2(__dmul_rn(d, x.x), __dmul_rn(d, x.y)); }
+  __device__ static void acc_mul(Acc& a, C v, Acc g) {
+    a.x = __fma_rn(v, g.x, a.x);
+    a.y = __fma_rn(v, g.y, a.y);
+  }
+  __device__ static TY out(Acc a) { return a; }
+  __device__ static TY add_out(TY a, TY b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+};
+
+// y = r + i t for the rounded (re, im) values r = H_re x and t = H_im x of
+// one element, or r - i t (conj: the adjoint's H_re^T - i H_im^T)
+__device__ __forceinline__ float2 cx_comb(float2 r, float2 t, bool conj) {
+  return conj ? make_float2(__fadd_rn(r.x, t.y), __fsub_rn(r.y, t.x))
+              : make_float2(__fsub_rn(r.x, t.y), __fadd_rn(r.y, t.x));
+}
+__device__ __forceinline__ double2 cx_comb(double2 r, double2 t, bool conj) {
+  return conj ? make_double2(__dadd_rn(r.x, t.y), __dsub_rn(r.y, t.x))
+              : make_double2(__dsub_rn(r.x, t.y), __dadd_rn(r.y, t.x));
+}
 
 // digit of a high (tile-uniform) site, held by lane (site % 32) in nh0/nh1
 __device__ __forceinline__ int high_digit(int site, int nh0, int nh1) {

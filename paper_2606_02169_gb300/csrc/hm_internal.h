@@ -320,6 +320,10 @@ struct Plan {
 
   // autotuned launch choice per (dtype, nvec); absent = default
   std::map<std::pair<int, long long>, TuneCfg> tuned;
+  // complex H: the form the autotuner measured fastest per (dtype, nvec):
+  // 0 the one-pass complex kernel, 1 its register-capped variant, 2 two
+  // tuned real passes and the combine
+  std::map<std::pair<int, long long>, int> cx_form;
 
   // batch handle
   bool is_batch = false;
@@ -404,7 +408,14 @@ int split_vector(const void* x, long long n, cudaStream_t s, Scratch& b, const f
 void df_window(double cmin, double cmax, double* lo, double* hi);
 // y = H x (or H^dagger x when adjoint) for nvec complex right-hand sides of a
 // complex plan, dt the real type of the (re, im) pairs
-int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s);
+// Complex H (this plan H_re, p->im H_im) on nvec complex right-hand sides
+// (dt the real dtype of their parts). mode 0: the form hm_tune chose (else
+// kCxDefaultForm), two passes where the one-pass kernel is not available;
+// 1: two passes of the general kernel's default launch; 2: the one-pass
+// kernel (cap: its register-capped variant) or HM_ERR_UNSUPPORTED; 3: two
+// passes with each part's tuned launch. native: FP64 arithmetic throughout.
+int apply_complex(Plan* p, bool adjoint, const void* x, void* y, long long nvec, hm_dtype dt, cudaStream_t s,
+                  int mode = 0, bool native = false, int ctas = 0, bool cap = false);
 int launch_adjoint(Plan* p, const void* gy, const void* x, void* gx, double* gcoef,
                    long long nvec, hm_dtype dt, cudaStream_t s);
 // Lanczos on vectors of vec_states * nvec elements of the real dtype dt

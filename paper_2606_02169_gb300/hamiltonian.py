@@ -138,6 +138,8 @@ class Hamiltonian:
         split: top-site split into two passes; split_sites: its number of
         leading sites (0 = chosen from the vector size). vinv: one group
         factor per lane where the plan allows it.
+        A complex H takes native_f64, transpose (H^dagger), mb (the register-capped one-pass kernel) and
+        scalar (two real passes instead of the one-pass complex kernel).
         presplit (timing diagnostic): x is a float32 tensor of 2 * D *
         nvec (hi, lo) pairs of FP64 values and out a float64 tensor; only the
         double-float apply kernel runs."""
@@ -217,14 +219,17 @@ class Hamiltonian:
         return self.tuned_config(nvec, dtype)
 
     def tuned_config(self, nvec: int = 1, dtype=torch.float64):
-        """dict(ctas, s, mb, small, prefetch, scalar, split, vinv, split_sites, kernel) of the stored launch choice (0 =
-        library default; kernel 1 = general, 2 = tile, 3 = staged)."""
+        """dict(ctas, s, mb, small, prefetch, scalar, split, vinv, split_sites, kernel, one_pass, one_pass_capped)
+        of the stored launch choice (0 = library default; kernel 1 = general, 2 = tile, 3 = staged; one_pass: a
+        complex H asked with a complex dtype runs the one-pass complex kernel, one_pass_capped its register-capped
+        variant, instead of two tuned real passes)."""
         code = _dtype_code(dtype)
         out = (ctypes.c_int32 * 4)()
         C.check(self._lib.hm_tuned_config(self._h, int(nvec), code, out), "hm_tuned_config")
         return {"ctas": out[0], "s": out[1], "mb": out[2] & 1, "small": (out[2] >> 1) & 1,
                 "prefetch": (out[2] >> 2) & 1, "scalar": (out[2] >> 3) & 1, "split": (out[2] >> 4) & 1,
-                "vinv": (out[2] >> 5) & 1, "split_sites": (out[2] >> 8) & 15, "kernel": out[3]}
+                "vinv": (out[2] >> 5) & 1, "split_sites": (out[2] >> 8) & 15, "kernel": out[3],
+                "one_pass": (out[2] >> 6) & 1, "one_pass_capped": (out[2] >> 7) & 1}
 
 
 class Batch:

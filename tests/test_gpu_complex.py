@@ -337,8 +337,11 @@ def test_complex_h_errors():
         h.apply(xr)
     assert e.value.code == C.HM_ERR_COMPLEX_REQUIRED
     with pytest.raises(HmError) as e:
-        h.apply_ex(xc)
+        h.apply_ex(xc, prefetch=True)          # complex H: bits 0, 1, 4 and 13 only
     assert e.value.code == C.HM_ERR_UNSUPPORTED
+    with pytest.raises(HmError) as e:
+        h.apply_ex(xr)
+    assert e.value.code == C.HM_ERR_COMPLEX_REQUIRED
     with pytest.raises(HmError) as e:
         h.adjoint(xc, xc)
     assert e.value.code == C.HM_ERR_UNSUPPORTED
