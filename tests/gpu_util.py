@@ -42,6 +42,43 @@ def abs_bound(model, x):
     return np.asarray(H @ xs).reshape(-1)
 
 
+def abs_terms(model):
+    """A term list whose operators have non-negative matrix elements that
+    bound each term's |c_t| |O_t| elementwise: Sy -> Sx (|Sy| equals Sx
+    elementwise), Sz on a spin-s site -> s I (|m| <= s, exact for s = 1/2);
+    the other operators (Sx, S+-, Sz^2, S+-^2, N, a, adag, I) are
+    non-negative already."""
+    out = []
+    for (i, oi, j, oj, c) in model.terms:
+        f = abs(c)
+        ops = []
+        for site, op in ((i, oi), (j, oj)):
+            if site >= 0:
+                kind, d = model.sites[site]
+                if op == "Sy":
+                    op = "Sx"
+                elif op == "Sz":
+                    f *= (d - 1) / 2.0
+                    op = "I"
+            ops.append((site, op))
+        out.append((ops[0][0], ops[0][1], ops[1][0], ops[1][1], f))
+    return out
+
+
+def row_abs_bound(model, x, rows):
+    """sum_t |c_t| (|O_t| |x|)_F for the sampled rows F (an upper bound on the
+    per-term error scale, from the row-wise oracle on |x|): the tolerance
+    scale of sampled rows of vectors held on the host."""
+    return np.abs(oracle.rows(model.sites, abs_terms(model), np.abs(np.asarray(x, dtype=np.float64)), rows).real)
+
+
+def apply_abs_bound(model, x, nvec=1):
+    """The same bound for every element of x (nvec right-hand sides), from
+    the row-wise oracle's full apply on |x|."""
+    xa = np.abs(np.asarray(x, dtype=np.float64))
+    return np.abs(oracle.apply(model.sites, abs_terms(model), xa, nvec=nvec).real)
+
+
 def row_scale_bound(model, xmax):
     """Crude per-row bound sum_t |c_t| max|O_t| * max|x| for sampled rows of
     systems too large to assemble."""

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import TOL_F32, TOL_F64, abs_bound, check_close, ham, row_scale_bound, torch_cuda
+from gpu_util import TOL_F32, TOL_F64, abs_bound, apply_abs_bound, check_close, ham, row_abs_bound, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -30,9 +30,10 @@ SMALL = [
 
 def _scale(m, x):
     """(|H||x|)_F where the Kronecker assembly is cheap; for a site of several
-    thousand levels (dense local matrices) the crude per-row bound."""
+    thousand levels (dense local matrices) the per-term bound from the
+    row-wise oracle on |x|."""
     if max(m.dims) > 1024:
-        return np.full(x.size, row_scale_bound(m, np.abs(x).max()))
+        return apply_abs_bound(m, x, nvec=x.size // oracle.dimension(m.sites))
     return abs_bound(m, x)
 
 
@@ -178,7 +179,7 @@ def sampled_parity(model, dtype, seed, n_random, tol):
     del x
     torch.cuda.empty_cache()
     ref = oracle.rows(model.sites, model.terms, xh, rows)
-    scale = np.full(rows.size, row_scale_bound(model, np.abs(xh).max()))
+    scale = row_abs_bound(model, xh, rows)
     return check_close(got, ref, scale, tol, model.name)
 
 

@@ -61,7 +61,7 @@ def test_batch_mixing_large_and_small_instances(dtype):
     kernel either way."""
     torch = torch_cuda()
     from paper_2606_02169_gb300 import Batch
-    from gpu_util import TOL_F64, row_scale_bound
+    from gpu_util import TOL_F64, apply_abs_bound
     models = [W.xxz_spin1_chain(13, seed=61)] + W.disorder_ensemble(count=5, nmin=3, nmax=7, base_seed=62) + \
         [W.xxz_spin1_chain(12, seed=63)]
     hams = [ham(m) for m in models]
@@ -75,7 +75,7 @@ def test_batch_mixing_large_and_small_instances(dtype):
     # the large instance against the oracle, every row
     xn = xs[0].double().cpu().numpy()
     ref = oracle.apply(models[0].sites, models[0].terms, xn, nvec=nvec)
-    scale = np.full(xn.size, row_scale_bound(models[0], np.abs(xn).max()))
+    scale = apply_abs_bound(models[0], xn, nvec=nvec)
     check_close(ys[0].double().cpu().numpy(), ref, scale, TOL_F32 if dtype == "f32" else TOL_F64, "large")
 
 
