@@ -125,3 +125,46 @@ def test_static_scratch_allocates_no_device_memory():
     free1, _ = torch.cuda.mem_get_info()
     assert torch.cuda.memory_allocated() == alloc0
     assert free1 == free0
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_static_scratch_gradients_in_a_cuda_graph(dtype):
+    """Captured into a CUDA graph (after one warm call) and replayed on new
+    gy and x copied into the captured buffers: each replay equals an
+    uncaptured call on those vectors bit for bit, and hm_apply_adjoint's
+    gradients within the FP64 tolerance (their grids differ)."""
+    torch = torch_cuda()
+    from paper_2606_02169_gb300 import Hamiltonian
+    lib, f = _entry()
+    tdt = getattr(torch, dtype)
+    code = 0 if dtype == "float64" else 1
+    m = W.square_lattice_xxz(3, 4, seed=4)
+    h = Hamiltonian(m.sites, m.terms)
+    gy = torch.from_numpy(W.vector(h.D, 7)).to("cuda", tdt)
+    x = torch.from_numpy(W.vector(h.D, 8)).to("cuda", tdt)
+    out = torch.empty(h.nterms, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):                       # warm call outside the capture
+        assert f(h.handle, gy.data_ptr(), x.data_ptr(), out.data_ptr(), 1, code, side.cuda_stream) == 0
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = f(h.handle, gy.data_ptr(), x.data_ptr(), out.data_ptr(), 1, code, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    for seed in (11, 12):
+        gy.copy_(torch.from_numpy(W.vector(h.D, seed)).to(tdt))
+        x.copy_(torch.from_numpy(W.vector(h.D, seed + 50)).to(tdt))
+        g.replay()
+        torch.cuda.synchronize()
+        got = out.clone()
+        direct = torch.full_like(out, float("nan"))
+        rc = f(h.handle, gy.data_ptr(), x.data_ptr(), direct.data_ptr(), 1, code,
+               torch.cuda.current_stream().cuda_stream)
+        assert rc == 0
+        _, ref = h.adjoint(gy, x, want_gx=False)
+        torch.cuda.synchronize()
+        assert torch.equal(got, direct), seed
+        r = ref.cpu().numpy()
+        assert np.allclose(got.cpu().numpy(), r, rtol=1e-11, atol=1e-13 * np.abs(r).max()), seed
