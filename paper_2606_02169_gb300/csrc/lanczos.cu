@@ -505,6 +505,77 @@ __global__ void k_caxpy(T* __restrict__ y, const T* __restrict__ v, double cr, d
   }
 }
 
+// y = sum_k (c_re[k] + i c_im[k]) v_k over a stored basis (v_k at B + k n),
+// in one pass: per element the same operations in the same order as me
+// k_caxpy launches from y = 0, so the result is bit for bit theirs (the
+// rebuilt-basis path runs those launches)
+constexpr int kCombineMax = 128;  // the Krylov dimension limit of hm_evolve
+
+struct CombineCoefs {
+  double c[2 * kCombineMax];
+  int me;
+};
+
+// (re, im) pair i of a vector in the library's basis allocation (aligned)
+__device__ __forceinline__ void ld_pair(const float* v, long long i, float& r, float& m) {
+  const float2 p = __ldcs(reinterpret_cast<const float2*>(v) + i);
+  r = p.x;
+  m = p.y;
+}
+__device__ __forceinline__ void ld_pair(const double* v, long long i, double& r, double& m) {
+  const double2 p = __ldcs(reinterpret_cast<const double2*>(v) + i);
+  r = p.x;
+  m = p.y;
+}
+
+// Each thread owns kCombinePairs pairs a block's width apart and walks the
+// basis once for all of them (that many independent 8- or 16-byte loads in
+// flight per vector).
+constexpr int kCombinePairs = 4;
+
+template <class T>
+__device__ __forceinline__ void caxpy_one(T& yr, T& yi, double cr, double ci, T vr, T vi) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 pr = pair_of(cr), pi = pair_of(ci), mpi = pair_of(-ci);
+    yr = lin3(yr, pr, vr, mpi, vi);
+    yi = lin3(yi, pr, vi, pi, vr);
+  } else {
+    yr = fma(cr, vr, fma(-ci, vi, yr));
+    yi = fma(cr, vi, fma(ci, vr, yi));
+  }
+}
+
+template <class T>
+__global__ void k_ccombine(T* __restrict__ y, const T* __restrict__ B, long long n, const CombineCoefs cc) {
+  constexpr int P = kCombinePairs;
+  const long long npairs = n / 2;
+  const long long span = (long long)blockDim.x * P;
+  for (long long base = blockIdx.x * span + threadIdx.x; base < npairs; base += (long long)gridDim.x * span) {
+    T yr[P], yi[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) yr[j] = yi[j] = T(0);
+    for (int k = 0; k < cc.me; ++k) {
+      const double cr = cc.c[2 * k], ci = cc.c[2 * k + 1];
+      const T* __restrict__ v = B + (size_t)k * n;
+      T vr[P], vi[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        if (base + j * blockDim.x < npairs) ld_pair(v, base + j * blockDim.x, vr[j], vi[j]);
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+        if (base + j * blockDim.x < npairs) caxpy_one(yr[j], yi[j], cr, ci, vr[j], vi[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const long long i = base + j * blockDim.x;
+      if (i < npairs) {
+        y[2 * i] = yr[j];
+        y[2 * i + 1] = yi[j];
+      }
+    }
+  }
+}
+
 // Eigendecomposition of the real symmetric tridiagonal T (diagonal a,
 // off-diagonal b) by the cyclic Jacobi method: rotations in the (p, q)
 // plane with tan t the smaller root of t^2 + 2 t theta - 1 = 0, theta =
@@ -629,11 +700,17 @@ static int evolve_t(Plan* p, const T* x, T* y, double t, int m, int nsub, int fl
     std::vector<double> a(ha.begin(), ha.begin() + me), b(hb.begin(), hb.begin() + (me - 1)), c;
     krylov_coeffs(a, b, tau, nu, c);
     if (me == m) esum += hb[m - 1] * std::hypot(c[2 * (m - 1)], c[2 * (m - 1) + 1]);
-    cudaMemsetAsync(out, 0, sizeof(T) * n, s);
-    if (B) {
+    if (B && me <= kCombineMax) {
+      CombineCoefs cc{};
+      for (int k = 0; k < 2 * me; ++k) cc.c[k] = c[k];
+      cc.me = me;
+      k_ccombine<T><<<R.vb, 256, 0, s>>>(out, B, n, cc);
+    } else if (B) {
+      cudaMemsetAsync(out, 0, sizeof(T) * n, s);
       for (int k = 0; k < me; ++k)
         k_caxpy<T><<<R.vb, 256, 0, s>>>(out, B + (size_t)k * n, c[2 * k], c[2 * k + 1], n / 2);
     } else {  // second pass of the same recurrence: the same v_k, bit for bit
+      cudaMemsetAsync(out, 0, sizeof(T) * n, s);
       rc = R.run(u, me, false, [&](int k, const T* vk) -> int {
         k_caxpy<T><<<R.vb, 256, 0, s>>>(out, vk, c[2 * k], c[2 * k + 1], n / 2);
         return HM_OK;
